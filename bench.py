@@ -1,0 +1,358 @@
+"""Benchmark: Swendsen-Wang sweeps of the periodic L = 16384 Ising lattice at
+beta_c (hot start, seed 7) on one GB300, through the library's C ABI.
+
+One step = one full sweep (activation, tile labeling, seam merge, root
+compression with root draws, flip with observables).  Prints one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the serial CPU oracle (the only reference this
+method has) on a bounded sample of the same workload.  With N > 1 (torchrun)
+every rank runs an independent replica (seed 7 + rank): the method does not
+shard, so scaling is weak and there is no collective on the data path.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+KC_ISING = 0.5 * math.log(1.0 + math.sqrt(2.0))
+L_BENCH, Q_BENCH, SEED_BENCH = 16384, 2, 7
+# the paper's number for this metric and workload: q = 2 at beta_c, L = 16384,
+# self-labeling + sewing on a Tesla M2070, 3.573 ns per site and sweep (Table I)
+PAPER_SITE_UPDATES_PER_NS = 1.0 / 3.573
+WORKLOAD = "sw_ising_q2_L16384_beta_c_hot_start_seed7"
+# algorithmic bytes per site of the tile-labeling kernel: read the 2-bit mask
+# (0.25 B) and write one int32 label (4 B)
+TILE_LABEL_BYTES_PER_SITE = 4.25
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_id), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def stop(self, t0, t1):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = [l for (t, l) in self.lines if t0 - 0.1 <= t <= t1 + 0.1] or [l for (_, l) in self.lines[-3:]]
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            p = [x.strip() for x in r.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_sample(seconds=15.0, L=4096):
+    """The serial oracle on this host: SW sweeps of an L x L sample of the
+    workload (same q, beta, seed) for about `seconds`.  Returns the dict for
+    the cpu_baseline key."""
+    import oracle
+    T = oracle.threshold(oracle.coupling_K(Q_BENCH, KC_ISING, 1.0, oracle.CONV_ISING))
+    s = oracle.init_spins(L, Q_BENCH, SEED_BENCH, True)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        s, _ = oracle.chain(L, Q_BENCH, T, SEED_BENCH, n, 1, s)
+        n += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": L * L * n / (dt * 1e9), "unit": "site-updates/ns", "cores": 1, "kind": "oracle",
+            "sample": "serial C oracle, %d SW sweeps of the L=%d q=2 Ising lattice at beta_c (hot start, "
+                      "seed 7) on one host core, %.1f s" % (n, L, dt),
+            "cpu": _cpu_model(), "host_cores": os.cpu_count()}
+
+
+def _cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def run_reference(args):
+    """--impl reference: the oracle on the host cores, each step one sweep of
+    an L = 1024 sample of the workload (same q, beta_c, hot start, seed)."""
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    L = 1024
+    T = oracle.threshold(oracle.coupling_K(Q_BENCH, KC_ISING, 1.0, oracle.CONV_ISING))
+    s = oracle.init_spins(L, Q_BENCH, SEED_BENCH, True)
+    for k in range(args.warmup):
+        s, _ = oracle.chain(L, Q_BENCH, T, SEED_BENCH, k, 1, s)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        s, _ = oracle.chain(L, Q_BENCH, T, SEED_BENCH, args.warmup + k, 1, s)
+    dt = time.perf_counter() - t0
+    value = L * L * args.steps / (dt * 1e9)
+    line = {
+        "impl": "reference", "metric": "SW site-updates/ns", "value": value, "unit": "site-updates/ns",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / max(args.steps, 1), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "L": L_BENCH, "q": Q_BENCH, "beta": KC_ISING,
+                   "sample_L": L, "note": "each step is one oracle sweep of an L=1024 sample"},
+        "cpu_baseline": {"value": value, "unit": "site-updates/ns", "cores": 1, "kind": "oracle",
+                         "sample": "one serial oracle sweep of the L=1024 q=2 Ising lattice at beta_c per step",
+                         "cpu": _cpu_model()},
+        "e2e": {"value": value, "unit": "site-updates/ns", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def ccl_secondary(torch, sw, n_seeds=20):
+    """Labeling workload: periodic 4096^2 critical percolation masks; each
+    label call timed alone with events, L2 flushed in between."""
+    H = W = 4096
+    N = H * W
+    masks = torch.empty((n_seeds, sw.mask_bytes(N)), dtype=torch.uint8, device="cuda")
+    for k in range(n_seeds):
+        sw.ccl_perc_mask(k, masks[k], H, W)
+    lab = torch.empty(N, dtype=torch.int32, device="cuda")
+    ws = torch.empty(sw.ccl_workspace_bytes(H, W), dtype=torch.uint8, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    st = torch.cuda.current_stream()
+    for k in range(3):
+        sw.ccl_label_ws(masks[k], lab, H, W, True, ws)
+    times = []
+    for k in range(n_seeds):
+        flush.fill_(k & 0xFF)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        sw.ccl_label_ws(masks[k], lab, H, W, True, ws)
+        b.record(st)
+        times.append((a, b))
+    torch.cuda.synchronize()
+    sw.ccl_status()
+    ms = sum(a.elapsed_time(b) for a, b in times)
+    return {"metric": "CCL Gsites/s", "workload": "ccl_perc_p0.5_periodic_4096x4096_seeds0-%d" % (n_seeds - 1),
+            "value": N * n_seeds / (ms * 1e-3) / 1e9, "unit": "Gsites/s", "ms_per_label": ms / n_seeds,
+            "l2": "flushed (256 MiB write) between labels"}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import paper_1105_5804_gb300 as sw
+    sw.lib()    # fails loudly when the extension is missing
+
+    L, q = L_BENCH, Q_BENCH
+    N = L * L
+    seed = SEED_BENCH + rank
+    h = sw.sw_create_ex(L, q, KC_ISING, 1.0, sw.SW_CONV_ISING, seed, True)
+    stream = torch.cuda.ExternalStream(sw.sw_stream(h))
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # warm-up (graph capture happens in the first call of graph mode)
+    sw.sw_sweep(h, max(args.warmup, 3))
+    sw.sw_sync(h)
+    sw.sw_observables(h, 4096)
+
+    # timed region: per-phase events on the handle's stream
+    sw.sw_set_timing(h, True)
+    sw.sw_phase_times(h)
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        uuid = local
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    t0 = time.time()
+    ev0.record(stream)
+    sw.sw_sweep(h, args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    barrier()
+    clk = clocks.stop(t0, t1)
+    ms = ev0.elapsed_time(ev1)
+    phases, n_timed = sw.sw_phase_times(h)
+    sw.sw_set_timing(h, False)
+    obs = sw.sw_observables(h, 4096)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * N * args.steps / (ms * 1e6)
+
+    # end to end through the C ABI with host buffers: upload spins, one sweep,
+    # read observables and spins back, every step
+    e2e_steps = max(3, min(args.steps, 20))
+    host_in = torch.empty(N, dtype=torch.int8).pin_memory()
+    host_out = torch.empty(N, dtype=torch.int8).pin_memory()
+    sw.sw_get_spins(h, host_in.numpy())    # warm the copies
+    barrier()
+    torch.cuda.synchronize()
+    te0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sw.sw_set_spins(h, host_in.numpy())
+        sw.sw_sweep(h, 1)
+        o = sw.sw_observables(h, 1)
+        sw.sw_get_spins(h, host_out.numpy())
+    te = time.perf_counter() - te0
+    if world > 1:
+        t = torch.tensor([te], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        te = float(t.item())
+    e2e_value = world * N * e2e_steps / (te * 1e9)
+
+    secondary = {}
+    if rank == 0 and not args.no_secondary:
+        secondary["ccl"] = ccl_secondary(torch, sw)
+        h4 = sw.sw_create_ex(L, 4, math.log(3.0), 1.0, sw.SW_CONV_POTTS, SEED_BENCH, True)
+        sw.sw_sweep(h4, 10)
+        s4 = torch.cuda.ExternalStream(sw.sw_stream(h4))
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(s4)
+        sw.sw_sweep(h4, 50)
+        b.record(s4)
+        torch.cuda.synchronize()
+        secondary["sw_potts_q4_L16384"] = {"value": N * 50 / (a.elapsed_time(b) * 1e6),
+                                           "unit": "site-updates/ns", "beta": math.log(3.0), "sweeps": 50}
+        sw.sw_destroy(h4)
+    sw.sw_destroy(h)
+
+    if rank != 0:
+        return
+    peak, peak_kind = _peaks()
+    local_ms = phases["local"] / max(n_timed, 1)
+    achieved = TILE_LABEL_BYTES_PER_SITE * N / (local_ms * 1e-3) / 1e9
+    mean_n_eq = float(obs[:, 0].mean()) if len(obs) else None
+    line = {
+        "metric": "SW site-updates/ns", "value": value, "unit": "site-updates/ns", "n_gpus": world,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": value / PAPER_SITE_UPDATES_PER_NS,
+        "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "L": L, "q": q, "beta": KC_ISING, "convention": "ising (K=2 beta J)",
+                   "start": "hot", "seed": SEED_BENCH, "replicas": world, "parallelism": "replicas",
+                   "l2": "inputs larger than L2 (int32 labels 1 GiB, spins 256 MiB per replica)"},
+        "clocks": clk,
+        "gpu_launches": 6 * args.steps,
+        "e2e": {"value": e2e_value, "unit": "site-updates/ns", "h2d_bytes_per_step": N,
+                "d2h_bytes_per_step": N + 8 * (q + 1), "steps": e2e_steps,
+                "path": "sw_set_spins(host) + sw_sweep(1) + sw_observables + sw_get_spins(host), pinned buffers"},
+        "roofline": {"bound": "hbm", "kernel": "k_tile_label", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "peak_kind": peak_kind,
+                     "bytes_model": "%.2f B/site (mask 0.25 read + int32 label 4 write) x %d sites per launch"
+                                    % (TILE_LABEL_BYTES_PER_SITE, N)},
+        "phase_ms_per_sweep": {k: v / max(n_timed, 1) for k, v in phases.items()},
+        "mean_n_eq_per_site": mean_n_eq / N if mean_n_eq else None,
+        "secondary": secondary,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sample(args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

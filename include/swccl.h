@@ -1,0 +1,207 @@
+/*
+ * swccl.h -- C ABI of libswccl.so: Swendsen-Wang cluster updates of the
+ * q-state Potts model and connected-component labeling of bond graphs on
+ * periodic or open 2D square grids, on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Weigel, "Connected component identification and cluster update on
+ * GPU", arXiv:1105.5804.  The Swendsen-Wang sweep (Sec. II, the three-step
+ * list after Eq. 5) is
+ *   1. activation: a bond joining equal spins opens with probability
+ *      p = 1 - exp(-K) (Sec. II below Eq. 4; rule of Eq. 7, Sec. II.A);
+ *   2. identification of the connected components of the open-bond graph
+ *      (Sec. II.B, II.C);
+ *   3. a new uniformly random state for every component (Sec. II.D).
+ *
+ * Conventions (the paper leaves them open; every one is fixed here):
+ *   - site index i = y*W + x (row-major); east of (x,y) is (x+1,y), north is
+ *     (x,y+1); with periodic boundaries both wrap.
+ *   - packed bond mask: byte i>>2 holds site i in bit 2*(i&3) (its east bond)
+ *     and bit 2*(i&3)+1 (its north bond); ceil(N/4) bytes for N sites.
+ *   - canonical labels: every site receives the smallest site index of its
+ *     cluster (the label BFS gives when it seeds clusters in site order,
+ *     Sec. II.B.1), so exactly one labeling is correct.
+ *   - spins: int8 values 0..q-1; the Ising sigma = 1 - 2s for q = 2.
+ *   - random numbers: Philox4x32-10 (Salmon et al., SC'11), counter based,
+ *     key = (seed_lo32, seed_hi32), counter = (c0, sweep_lo32, sweep_hi32, tag):
+ *       BOND (tag 0): c0 = i>>1, word 2*(i&1) + dir (dir 0 east, 1 north);
+ *       FLIP (tag 1): c0 = root (canonical label), word 0;
+ *       INIT (tag 2): c0 = i, word 0, sweep 0;
+ *       PERC (tag 3): key = (k, 0), sweep 0, words as BOND.
+ *     A bond between equal spins opens iff r < T with the 32-bit threshold
+ *     T = min(2^32, floor(p 2^32)) computed in IEEE double on the host;
+ *     a cluster's new state is floor(r q / 2^32).
+ *   - coupling: K = beta*J for the Potts delta convention (Eq. 1),
+ *     K = 2*beta*J for +-1 Ising spins; SW_CONV_AUTO picks Ising for q = 2
+ *     and Potts otherwise.  Both give p_c = sqrt(q)/(1+sqrt(q)) at the
+ *     critical point.
+ *
+ * Threads: calls on different handles may run on different host threads.
+ * One handle must not be used from two host threads at once.
+ *
+ * Errors: every int-returning call returns SW_OK (0) or one of the codes
+ * below and sets a per-thread message readable with sw_last_error().
+ * Kernels never trap: a device-side check that fails (an iteration bound
+ * exceeded, which only corrupted buffers can cause) records SW_ERR_STATE in
+ * a status word that the next synchronising call reports.
+ */
+#ifndef SWCCL_H
+#define SWCCL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SW_OK 0
+#define SW_ERR_ARG 1     /* invalid argument; nothing was launched           */
+#define SW_ERR_OOM 2     /* device or host allocation failed                 */
+#define SW_ERR_CUDA 3    /* a CUDA runtime call failed (message has details) */
+#define SW_ERR_TIMEOUT 4 /* a bounded device wait ran out                    */
+#define SW_ERR_STATE 5   /* a device-side consistency check failed           */
+
+#define SW_CONV_AUTO 0   /* Ising (K = 2 beta J) for q = 2, Potts otherwise  */
+#define SW_CONV_POTTS 1  /* delta coupling, Eq. 1: K = beta J                */
+#define SW_CONV_ISING 2  /* +-1 spins: K = 2 beta J                          */
+
+/* Phases timed by sw_phase_times(), in launch order. */
+#define SW_PHASE_ACTIVATE 0  /* bond activation                 (Sec. II.A)   */
+#define SW_PHASE_LOCAL 1     /* tile-local labeling             (Sec. II.B)   */
+#define SW_PHASE_MERGE 2     /* union of roots across tile seams (Sec. II.C)  */
+#define SW_PHASE_ROOTS 3     /* root compression + root draws   (Sec. II.C/D) */
+#define SW_PHASE_FLIP 4      /* cluster flip + observables      (Sec. II.D)   */
+#define SW_N_PHASES 5
+
+typedef struct sw_handle sw_handle;
+
+/* Message of the last failed call on this host thread ("" if none).  The
+ * string is owned by the library and stays valid until the next call. */
+const char* sw_last_error(void);
+
+/* The 32-bit activation threshold T for (q, beta, J, convention), as the
+ * create calls compute it: T = min(2^32, floor((1 - exp(-K)) 2^32)).
+ * Returns 0 for K <= 0. */
+uint64_t sw_threshold_for(int q, double beta, double J, int convention);
+
+/* ------------------------------------------------------------------------ */
+/* Swendsen-Wang chain on one periodic L x L lattice                         */
+/* ------------------------------------------------------------------------ */
+
+/* Create a chain: L x L periodic lattice, q states, inverse temperature beta,
+ * J = 1, SW_CONV_AUTO, cold start (every s = 0), its own CUDA stream.
+ * Requirements: 4 <= L <= 46340, L % 4 == 0; 2 <= q <= 127; beta >= 0.
+ * The library owns all device memory of the chain (spins, mask, labels,
+ * root lists, seam records, a ring of per-sweep observables); about
+ * 10.5 bytes per site.  Returns NULL on failure (see sw_last_error()). */
+sw_handle* sw_create(int L, int q, double beta, uint64_t seed);
+
+/* As sw_create with explicit coupling J, convention (SW_CONV_*), hot start
+ * (hot_start != 0: s_i = floor(r q / 2^32) from the INIT draw) and stream
+ * (a cudaStream_t; NULL makes the handle create its own non-blocking stream).
+ * All work of the handle is ordered on that stream. */
+sw_handle* sw_create_ex(int L, int q, double beta, double J, int convention, uint64_t seed,
+                        int hot_start, void* stream);
+
+/* As sw_create_ex with the threshold given directly, 0 <= T <= 2^32 (tests;
+ * T = 2^32 opens every bond between equal spins). */
+sw_handle* sw_create_threshold(int L, int q, uint64_t T, uint64_t seed, int hot_start, void* stream);
+
+/* Free every device resource of the handle (waits for its stream first).
+ * NULL is accepted. */
+int sw_destroy(sw_handle* h);
+
+/* Enqueue n >= 0 sweeps (Sec. II: activate, identify, flip) on the handle's
+ * stream and return without waiting.  Sweep k of the chain (k = 0 for the
+ * first sweep after create) draws its bonds and flips with sweep index k.
+ * After each sweep the observables (n_eq, n_0..n_{q-1}) of the new spins
+ * are stored in a device ring of the last 4096 sweeps. */
+int sw_sweep(sw_handle* h, int n);
+
+/* Wait for the handle's stream; report SW_ERR_STATE if a device check failed. */
+int sw_sync(sw_handle* h);
+
+/* Copy observables of sweeps not yet read, oldest first, to host memory:
+ * out[k*(1+q) + 0] = n_eq = number of lattice bonds joining equal spins
+ * (H = -J n_eq in the Potts convention of Eq. 1; E = -J (2 n_eq - 2N) for
+ * Ising), out[k*(1+q) + 1 + s] = number of sites in state s.  At most
+ * max_sweeps entries are written; *n_written receives the count.  Entries
+ * older than the ring (4096 sweeps) are dropped.  Synchronises the stream. */
+int sw_observables(sw_handle* h, int64_t* out, int max_sweeps, int* n_written);
+
+/* Copy the current spins (int8[L*L], row-major) out, to host memory
+ * (is_device == 0) or device memory (is_device != 0).  Synchronises. */
+int sw_get_spins(sw_handle* h, int8_t* dst, int is_device);
+
+/* Replace the current spins from host (is_device == 0) or device memory;
+ * values must be in [0, q): otherwise SW_ERR_ARG and the spins are left
+ * unchanged.  Host input is copied into the handle's label buffer and
+ * checked on the device, so sw_debug_dump has nothing to report until the
+ * next sweep.  Synchronises. */
+int sw_set_spins(sw_handle* h, const int8_t* src, int is_device);
+
+/* Copy the bond mask (ceil(L*L/4) bytes, packed as above) and the canonical
+ * labels (int32[L*L]) of the last completed sweep, for bit-exact checks.
+ * Either pointer may be NULL.  SW_ERR_STATE if no sweep ran since creation
+ * or since the last host sw_set_spins.  Synchronises. */
+int sw_debug_dump(sw_handle* h, uint8_t* mask_out, int32_t* labels_out, int is_device);
+
+/* info[0..7] = L, q, T, seed, sweeps enqueued so far, observable ring
+ * capacity, tile height, tile width. */
+int sw_get_info(sw_handle* h, int64_t* info);
+
+/* The CUDA stream (cudaStream_t) all work of the handle is ordered on. */
+void* sw_stream(sw_handle* h);
+
+/* Per-phase timing.  With timing on, sw_sweep launches each phase directly
+ * with CUDA events between phases (no graph); with it off (default) one
+ * sweep is a captured CUDA graph.  Both compute the same chain. */
+int sw_set_timing(sw_handle* h, int enable);
+
+/* Milliseconds spent in each phase (ms[SW_N_PHASES]) summed over the sweeps
+ * timed since the last call, and their number.  Synchronises and resets. */
+int sw_phase_times(sw_handle* h, double* ms, int64_t* n_sweeps);
+
+/* ------------------------------------------------------------------------ */
+/* Connected-component labeling of a bond mask (Sec. II.B, II.C)             */
+/* ------------------------------------------------------------------------ */
+
+/* Label the clusters of the open-bond graph of an H x W grid.
+ * bond_mask: device pointer, ceil(H*W/4) bytes, packed layout above.
+ * labels: device pointer, int32[H*W]; receives canonical labels.
+ * periodic != 0: east/north bonds of the last column/row wrap around;
+ * periodic == 0: those bonds are ignored (image segmentation).
+ * Requires H, W >= 1 and H*W < 2^31.  Enqueued on `stream` (a
+ * cudaStream_t, NULL = legacy default stream); returns without waiting.
+ * Scratch memory (about 4.1 bytes per site) is taken with cudaMallocAsync
+ * on the same stream and released in stream order. */
+int ccl_label(const uint8_t* bond_mask, int32_t* labels, int H, int W, int periodic, void* stream);
+
+/* Bytes of scratch ccl_label_ws needs for an H x W grid (-1 if invalid). */
+int64_t ccl_workspace_bytes(int H, int W);
+
+/* ccl_label with caller-owned scratch: `workspace` is a device pointer of
+ * at least ccl_workspace_bytes(H, W) bytes, 256-byte aligned.  Calls that
+ * share a workspace must be ordered (same stream or synchronised). */
+int ccl_label_ws(const uint8_t* bond_mask, int32_t* labels, int H, int W, int periodic,
+                 void* workspace, int64_t ws_bytes, void* stream);
+
+/* Bond mask of an image (Potts mapping of segmentation, Sec. I): a bond is
+ * open iff its two pixels have the same value.  px: device uint8[H*W];
+ * mask: device, ceil(H*W/4) bytes.  With periodic == 0 bonds leaving the
+ * grid are closed. */
+int ccl_bonds_from_pixels(const uint8_t* px, uint8_t* mask, int H, int W, int periodic, void* stream);
+
+/* Critical bond percolation mask (p = 1/2) of seed k: each of the 2*H*W
+ * bond bits is open iff its PERC draw is below 2^31.  mask: device,
+ * ceil(H*W/4) bytes. */
+int ccl_perc_mask(uint64_t k, uint8_t* mask, int H, int W, void* stream);
+
+/* Wait for the whole device and return the first device-side failure
+ * recorded by ccl_* kernels since the last call (SW_OK if none); clears it. */
+int ccl_status(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SWCCL_H */

@@ -1,0 +1,68 @@
+"""GB300-native Swendsen-Wang cluster updates and bond-graph labeling.
+
+Python binding of libswccl.so: the C ABI declared in ``include/swccl.h``
+(Weigel, arXiv:1105.5804: bond activation, cluster identification, cluster
+flip).  All computation runs in the library's sm_103a kernels; PyTorch only
+supplies device memory and streams.  Importing this package does not load the
+library; the first call does, and raises if it was not built.
+"""
+from ._lib import (  # noqa: F401
+    SW_OK, SW_ERR_ARG, SW_ERR_OOM, SW_ERR_CUDA, SW_ERR_TIMEOUT, SW_ERR_STATE,
+    SW_CONV_AUTO, SW_CONV_POTTS, SW_CONV_ISING, SW_N_PHASES, PHASE_NAMES,
+    SwcclError, lib, mask_bytes,
+    sw_last_error, sw_threshold_for, sw_create, sw_create_ex, sw_create_threshold, sw_destroy,
+    sw_sweep, sw_sync, sw_observables, sw_get_spins, sw_set_spins, sw_debug_dump, sw_get_info,
+    sw_stream, sw_set_timing, sw_phase_times,
+    ccl_label, ccl_workspace_bytes, ccl_label_ws, ccl_bonds_from_pixels, ccl_perc_mask, ccl_status,
+)
+
+
+class SwendsenWang:
+    """Owning wrapper of one chain handle (``sw_create_ex``)."""
+
+    def __init__(self, L, q, beta, seed, J=1.0, convention=SW_CONV_AUTO, hot_start=False,
+                 threshold=None, stream=0):
+        if threshold is None:
+            self.h = sw_create_ex(L, q, beta, J, convention, seed, hot_start, stream)
+        else:
+            self.h = sw_create_threshold(L, q, threshold, seed, hot_start, stream)
+        self.L, self.q = L, q
+
+    def sweep(self, n=1):
+        sw_sweep(self.h, n)
+
+    def observables(self, max_sweeps=4096):
+        return sw_observables(self.h, max_sweeps)
+
+    def spins(self, out=None):
+        return sw_get_spins(self.h, out)
+
+    def set_spins(self, src):
+        sw_set_spins(self.h, src)
+
+    def debug_dump(self):
+        return sw_debug_dump(self.h)
+
+    def info(self):
+        return sw_get_info(self.h)
+
+    @property
+    def stream(self):
+        return sw_stream(self.h)
+
+    def close(self):
+        if self.h:
+            sw_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,263 @@
+"""ctypes binding of libswccl.so (C ABI in include/swccl.h).
+
+Argument marshalling only: every step of the method runs in the CUDA
+kernels of the library.  Device buffers are passed as torch CUDA tensors
+(their ``data_ptr()``), streams as ``torch.cuda.Stream`` / raw handles.
+There is no fallback: if the library is not built, every call raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libswccl.so")
+
+SW_OK, SW_ERR_ARG, SW_ERR_OOM, SW_ERR_CUDA, SW_ERR_TIMEOUT, SW_ERR_STATE = 0, 1, 2, 3, 4, 5
+SW_CONV_AUTO, SW_CONV_POTTS, SW_CONV_ISING = 0, 1, 2
+SW_N_PHASES = 5
+PHASE_NAMES = ("activate", "local", "merge", "roots", "flip")
+
+
+class SwcclError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("swccl error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library.  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libswccl.so is not built (%s); run __graft_entry__.build() "
+                           "or python -m paper_1105_5804_gb300.build" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, u64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+    sig = {
+        "sw_last_error": ([], ctypes.c_char_p),
+        "sw_threshold_for": ([i32, dbl, dbl, i32], u64),
+        "sw_create": ([i32, i32, dbl, u64], vp),
+        "sw_create_ex": ([i32, i32, dbl, dbl, i32, u64, i32, vp], vp),
+        "sw_create_threshold": ([i32, i32, u64, u64, i32, vp], vp),
+        "sw_destroy": ([vp], i32),
+        "sw_sweep": ([vp, i32], i32),
+        "sw_sync": ([vp], i32),
+        "sw_observables": ([vp, vp, i32, ctypes.POINTER(i32)], i32),
+        "sw_get_spins": ([vp, vp, i32], i32),
+        "sw_set_spins": ([vp, vp, i32], i32),
+        "sw_debug_dump": ([vp, vp, vp, i32], i32),
+        "sw_get_info": ([vp, vp], i32),
+        "sw_stream": ([vp], vp),
+        "sw_set_timing": ([vp, i32], i32),
+        "sw_phase_times": ([vp, vp, ctypes.POINTER(i64)], i32),
+        "ccl_label": ([vp, vp, i32, i32, i32, vp], i32),
+        "ccl_workspace_bytes": ([i32, i32], i64),
+        "ccl_label_ws": ([vp, vp, i32, i32, i32, vp, i64, vp], i32),
+        "ccl_bonds_from_pixels": ([vp, vp, i32, i32, i32, vp], i32),
+        "ccl_perc_mask": ([u64, vp, i32, i32, vp], i32),
+        "ccl_status": ([], i32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return _lib
+
+
+def sw_last_error():
+    return lib().sw_last_error().decode()
+
+
+def _check(rc):
+    if rc != SW_OK:
+        raise SwcclError(rc, sw_last_error())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev(t, dtype, numel=None, name="tensor"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must have dtype %s" % (name, dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if numel is not None and t.numel() < numel:
+        raise ValueError("%s needs at least %d elements" % (name, numel))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def mask_bytes(n_sites):
+    return (n_sites + 3) // 4
+
+
+# ---------------------------------------------------------------------------
+# Swendsen-Wang chain
+# ---------------------------------------------------------------------------
+def sw_threshold_for(q, beta, J=1.0, convention=SW_CONV_AUTO):
+    return int(lib().sw_threshold_for(q, beta, J, convention))
+
+
+def _handle(h):
+    if not h:
+        raise SwcclError(SW_ERR_ARG, sw_last_error())
+    return h
+
+
+def sw_create(L, q, beta, seed):
+    return _handle(lib().sw_create(L, q, beta, seed))
+
+
+def sw_create_ex(L, q, beta, J, convention, seed, hot_start, stream=0):
+    return _handle(lib().sw_create_ex(L, q, beta, J, convention, seed, 1 if hot_start else 0,
+                                      _stream(stream) if stream else None))
+
+
+def sw_create_threshold(L, q, T, seed, hot_start, stream=0):
+    return _handle(lib().sw_create_threshold(L, q, T, seed, 1 if hot_start else 0,
+                                             _stream(stream) if stream else None))
+
+
+def sw_destroy(h):
+    _check(lib().sw_destroy(h))
+
+
+def sw_sweep(h, n):
+    _check(lib().sw_sweep(h, n))
+
+
+def sw_sync(h):
+    _check(lib().sw_sync(h))
+
+
+def sw_get_info(h):
+    info = np.zeros(8, dtype=np.int64)
+    _check(lib().sw_get_info(h, info.ctypes.data))
+    keys = ("L", "q", "T", "seed", "sweeps", "obs_capacity", "tile_h", "tile_w")
+    return {k: int(v) for k, v in zip(keys, info)}
+
+
+def sw_observables(h, max_sweeps=4096):
+    q = sw_get_info(h)["q"]
+    out = np.zeros((max_sweeps, 1 + q), dtype=np.int64)
+    n = ctypes.c_int(0)
+    _check(lib().sw_observables(h, out.ctypes.data, max_sweeps, ctypes.byref(n)))
+    return out[: n.value]
+
+
+def sw_get_spins(h, out=None):
+    """Current spins: into ``out`` (a host numpy int8 array or a CUDA int8
+    tensor) or into a new numpy array."""
+    info = sw_get_info(h)
+    N = info["L"] ** 2
+    if out is None or isinstance(out, np.ndarray):
+        a = np.empty(N, dtype=np.int8) if out is None else out
+        if a.dtype != np.int8 or a.size < N or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("out must be a contiguous int8 array of %d elements" % N)
+        _check(lib().sw_get_spins(h, a.ctypes.data, 0))
+        return a
+    import torch
+    _check(lib().sw_get_spins(h, _dev(out, torch.int8, N, "out"), 1))
+    return out
+
+
+def sw_set_spins(h, src):
+    import torch
+    N = sw_get_info(h)["L"] ** 2
+    if isinstance(src, torch.Tensor) and src.is_cuda:
+        _check(lib().sw_set_spins(h, _dev(src, torch.int8, N, "src"), 1))
+    else:
+        a = np.ascontiguousarray(src, dtype=np.int8).reshape(-1)
+        if a.size != N:
+            raise ValueError("need %d spins" % N)
+        _check(lib().sw_set_spins(h, a.ctypes.data, 0))
+
+
+def sw_debug_dump(h, mask_out=None, labels_out=None):
+    """(mask, labels) of the last sweep, as numpy arrays, or into CUDA tensors."""
+    import torch
+    N = sw_get_info(h)["L"] ** 2
+    if mask_out is None and labels_out is None:
+        m = np.empty(mask_bytes(N), dtype=np.uint8)
+        lab = np.empty(N, dtype=np.int32)
+        _check(lib().sw_debug_dump(h, m.ctypes.data, lab.ctypes.data, 0))
+        return m, lab
+    mp = _dev(mask_out, torch.uint8, mask_bytes(N), "mask_out") if mask_out is not None else None
+    lp = _dev(labels_out, torch.int32, N, "labels_out") if labels_out is not None else None
+    _check(lib().sw_debug_dump(h, mp, lp, 1))
+    return mask_out, labels_out
+
+
+def sw_stream(h):
+    return int(lib().sw_stream(h) or 0)
+
+
+def sw_set_timing(h, enable):
+    _check(lib().sw_set_timing(h, 1 if enable else 0))
+
+
+def sw_phase_times(h):
+    ms = np.zeros(SW_N_PHASES, dtype=np.float64)
+    n = ctypes.c_int64(0)
+    _check(lib().sw_phase_times(h, ms.ctypes.data, ctypes.byref(n)))
+    return dict(zip(PHASE_NAMES, ms.tolist())), int(n.value)
+
+
+# ---------------------------------------------------------------------------
+# Stand-alone labeling
+# ---------------------------------------------------------------------------
+def ccl_label(bond_mask, labels, H, W, periodic, stream=None):
+    import torch
+    N = H * W
+    _check(lib().ccl_label(_dev(bond_mask, torch.uint8, mask_bytes(N), "bond_mask"),
+                           _dev(labels, torch.int32, N, "labels"), H, W, 1 if periodic else 0,
+                           _stream(stream)))
+    return labels
+
+
+def ccl_workspace_bytes(H, W):
+    return int(lib().ccl_workspace_bytes(H, W))
+
+
+def ccl_label_ws(bond_mask, labels, H, W, periodic, workspace, stream=None):
+    import torch
+    N = H * W
+    _check(lib().ccl_label_ws(_dev(bond_mask, torch.uint8, mask_bytes(N), "bond_mask"),
+                              _dev(labels, torch.int32, N, "labels"), H, W, 1 if periodic else 0,
+                              _dev(workspace, torch.uint8, None, "workspace"), workspace.numel(),
+                              _stream(stream)))
+    return labels
+
+
+def ccl_bonds_from_pixels(px, mask, H, W, periodic, stream=None):
+    import torch
+    N = H * W
+    _check(lib().ccl_bonds_from_pixels(_dev(px, torch.uint8, N, "px"),
+                                       _dev(mask, torch.uint8, mask_bytes(N), "mask"), H, W,
+                                       1 if periodic else 0, _stream(stream)))
+    return mask
+
+
+def ccl_perc_mask(k, mask, H, W, stream=None):
+    import torch
+    _check(lib().ccl_perc_mask(k, _dev(mask, torch.uint8, mask_bytes(H * W), "mask"), H, W,
+                               _stream(stream)))
+    return mask
+
+
+def ccl_status():
+    _check(lib().ccl_status())

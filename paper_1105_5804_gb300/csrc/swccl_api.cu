@@ -1,0 +1,460 @@
+// swccl_api.cu -- host driver and C ABI of libswccl (declared in include/swccl.h).
+//
+// A Swendsen-Wang sweep (Sec. II, three steps) is five kernels on the
+// handle's stream: activation, tile labeling, seam merge, root compression
+// with root draws, flip with observables; a one-thread kernel then advances
+// the sweep counter held in device memory, so one captured CUDA graph serves
+// every sweep.  Nothing crosses to the host inside a sweep (the paper's
+// relaxation checked its stopping rule on the CPU between launches,
+// Sec. II.C.1; the atomic merge needs no such loop).
+#include <cmath>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "swccl_shared.h"
+
+using namespace swccl;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(SW_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+constexpr int OBS_CAP = 4096;
+
+}  // namespace
+
+// Device status word of the stand-alone labeling calls.
+__device__ int g_ccl_status;
+
+struct sw_handle {
+  int L = 0, q = 0;
+  uint64_t T = 0, seed = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  Grid grid{};
+  int8_t* spins = nullptr;
+  uint8_t* mask = nullptr;
+  int32_t* labels = nullptr;
+  void* scratch = nullptr;
+  LabelScratch ls{};
+  SwCtl* ctl = nullptr;
+  int* chk = nullptr;
+  int64_t* obs = nullptr;
+  uint64_t sweeps = 0;     // sweeps enqueued
+  uint64_t obs_read = 0;   // next sweep whose observables are unread
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool timing = false;
+  bool dump_valid = false;  // mask/labels hold the last sweep's result
+  std::vector<cudaEvent_t> ev_pending;   // SW_N_PHASES + 1 events per timed sweep
+  std::vector<cudaEvent_t> ev_free;
+};
+
+namespace {
+
+void free_handle(sw_handle* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->exec) cudaGraphExecDestroy(h->exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  for (auto e : h->ev_pending) cudaEventDestroy(e);
+  for (auto e : h->ev_free) cudaEventDestroy(e);
+  cudaFree(h->spins);
+  cudaFree(h->mask);
+  cudaFree(h->labels);
+  cudaFree(h->scratch);
+  cudaFree(h->ctl);
+  cudaFree(h->chk);
+  cudaFree(h->obs);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+// Enqueue one sweep.
+cudaError_t enqueue_sweep(sw_handle* h, cudaEvent_t* ev) {
+  cudaError_t e;
+  const cudaStream_t st = h->stream;
+  if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
+  if ((e = launch_activate(h->spins, h->mask, h->L, h->T, h->seed, h->ctl, h->obs, OBS_CAP, h->q, st)))
+    return e;
+  if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
+  if ((e = launch_tile_label(h->mask, h->labels, h->grid, h->ls, st))) return e;
+  if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
+  if ((e = launch_merge(h->labels, h->grid, h->ls, st))) return e;
+  if (ev && (e = cudaEventRecord(ev[3], st)) != cudaSuccess) return e;
+  if ((e = launch_root_compress(h->labels, h->grid, h->ls, h->spins, h->q, h->seed, h->ctl, st))) return e;
+  if (ev && (e = cudaEventRecord(ev[4], st)) != cudaSuccess) return e;
+  if ((e = launch_flip(h->spins, h->labels, h->L, h->q, h->ctl, h->obs, OBS_CAP, st))) return e;
+  if (ev && (e = cudaEventRecord(ev[5], st)) != cudaSuccess) return e;
+  return launch_advance(h->ctl, st);
+}
+
+int check_device_status(sw_handle* h) {
+  CK(cudaStreamSynchronize(h->stream));
+  SwCtl c;
+  CK(cudaMemcpy(&c, h->ctl, sizeof(c), cudaMemcpyDeviceToHost));
+  if (c.err) return fail(c.err, "a device-side consistency check failed in a sweep");
+  return SW_OK;
+}
+
+double coupling_K(int q, double beta, double J, int conv) {
+  if (conv == SW_CONV_AUTO) conv = (q == 2) ? SW_CONV_ISING : SW_CONV_POTTS;
+  return conv == SW_CONV_ISING ? 2.0 * beta * J : beta * J;
+}
+
+uint64_t threshold_of(double K) {
+  if (!(K > 0.0)) return 0;
+  const double p = -std::expm1(-K);
+  const double t = std::floor(p * 4294967296.0);
+  if (t >= 4294967296.0) return 1ull << 32;
+  if (t < 0.0) return 0;
+  return (uint64_t)t;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sw_last_error(void) { return g_err.c_str(); }
+
+uint64_t sw_threshold_for(int q, double beta, double J, int convention) {
+  return threshold_of(coupling_K(q, beta, J, convention));
+}
+
+sw_handle* sw_create_threshold(int L, int q, uint64_t T, uint64_t seed, int hot_start, void* stream) {
+  if (L < 4 || L > 46340 || L % 4 != 0) {
+    fail(SW_ERR_ARG, "sw_create: L must satisfy 4 <= L <= 46340 and L % 4 == 0");
+    return nullptr;
+  }
+  if (q < 2 || q > 127) {
+    fail(SW_ERR_ARG, "sw_create: q must be in [2, 127]");
+    return nullptr;
+  }
+  if (T > (1ull << 32)) {
+    fail(SW_ERR_ARG, "sw_create: threshold T must be <= 2^32");
+    return nullptr;
+  }
+  sw_handle* h = new sw_handle();
+  h->L = L;
+  h->q = q;
+  h->T = T;
+  h->seed = seed;
+  h->grid = make_grid(L, L, 1);
+  const int64_t N = (int64_t)L * L;
+  auto bad = [&](cudaError_t e, const char* what) -> sw_handle* {
+    cuda_fail(e, what);
+    if (e == cudaErrorMemoryAllocation) g_err = std::string("out of device memory: ") + what;
+    free_handle(h);
+    return nullptr;
+  };
+  cudaError_t e;
+  if ((e = cudaGetDevice(&h->device))) return bad(e, "cudaGetDevice");
+  if (stream) {
+    h->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    if ((e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking))) return bad(e, "cudaStreamCreate");
+    h->own_stream = true;
+  }
+  const int64_t sbytes = label_scratch_bytes(h->grid);
+  if ((e = cudaMalloc(&h->spins, (N + 15) & ~15LL))) return bad(e, "spins");
+  if ((e = cudaMalloc(&h->mask, ((N + 3) / 4 + 15) & ~15LL))) return bad(e, "mask");
+  if ((e = cudaMalloc(&h->labels, N * 4))) return bad(e, "labels");
+  if ((e = cudaMalloc(&h->scratch, sbytes))) return bad(e, "label scratch");
+  if ((e = cudaMalloc(&h->ctl, sizeof(SwCtl)))) return bad(e, "control block");
+  if ((e = cudaMalloc(&h->chk, sizeof(int)))) return bad(e, "check word");
+  if ((e = cudaMalloc(&h->obs, (int64_t)OBS_CAP * (q + 1) * 8))) return bad(e, "observable ring");
+  h->ls = carve_label_scratch(h->grid, h->scratch,
+                              reinterpret_cast<int*>(reinterpret_cast<char*>(h->ctl) + offsetof(SwCtl, err)));
+  if ((e = cudaMemsetAsync(h->ctl, 0, sizeof(SwCtl), h->stream))) return bad(e, "memset");
+  if ((e = cudaMemsetAsync(h->obs, 0, (int64_t)OBS_CAP * (q + 1) * 8, h->stream))) return bad(e, "memset");
+  if ((e = launch_init_spins(h->spins, L, q, seed, hot_start, h->stream))) return bad(e, "init spins");
+  if ((e = cudaStreamSynchronize(h->stream))) return bad(e, "sync");
+  g_err.clear();
+  return h;
+}
+
+sw_handle* sw_create_ex(int L, int q, double beta, double J, int convention, uint64_t seed,
+                        int hot_start, void* stream) {
+  if (!(beta >= 0.0) || !std::isfinite(beta) || !std::isfinite(J) || convention < 0 || convention > 2) {
+    fail(SW_ERR_ARG, "sw_create_ex: beta must be finite and >= 0, J finite, convention in {0,1,2}");
+    return nullptr;
+  }
+  return sw_create_threshold(L, q, threshold_of(coupling_K(q, beta, J, convention)), seed, hot_start, stream);
+}
+
+sw_handle* sw_create(int L, int q, double beta, uint64_t seed) {
+  return sw_create_ex(L, q, beta, 1.0, SW_CONV_AUTO, seed, 0, nullptr);
+}
+
+int sw_destroy(sw_handle* h) {
+  free_handle(h);
+  return SW_OK;
+}
+
+int sw_sweep(sw_handle* h, int n) {
+  if (!h) return fail(SW_ERR_ARG, "sw_sweep: null handle");
+  if (n < 0) return fail(SW_ERR_ARG, "sw_sweep: n must be >= 0");
+  if (h->timing) {
+    for (int k = 0; k < n; ++k) {
+      cudaEvent_t ev[SW_N_PHASES + 1];
+      for (auto& e : ev) {
+        if (!h->ev_free.empty()) {
+          e = h->ev_free.back();
+          h->ev_free.pop_back();
+        } else {
+          CK(cudaEventCreate(&e));
+        }
+        h->ev_pending.push_back(e);
+      }
+      CK(enqueue_sweep(h, ev));
+      h->sweeps++;
+      h->dump_valid = true;
+    }
+    return SW_OK;
+  }
+  if (!h->exec) {
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = enqueue_sweep(h, nullptr);
+    cudaGraph_t gr = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(h->stream, &gr);
+    if (e != cudaSuccess) { if (gr) cudaGraphDestroy(gr); return cuda_fail(e, "capture of one sweep"); }
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+    h->graph = gr;
+    CK(cudaGraphInstantiate(&h->exec, h->graph, 0));
+  }
+  for (int k = 0; k < n; ++k) {
+    CK(cudaGraphLaunch(h->exec, h->stream));
+    h->sweeps++;
+    h->dump_valid = true;
+  }
+  return SW_OK;
+}
+
+int sw_sync(sw_handle* h) {
+  if (!h) return fail(SW_ERR_ARG, "sw_sync: null handle");
+  return check_device_status(h);
+}
+
+int sw_observables(sw_handle* h, int64_t* out, int max_sweeps, int* n_written) {
+  if (!h || (!out && max_sweeps > 0) || max_sweeps < 0) return fail(SW_ERR_ARG, "sw_observables: bad arguments");
+  if (n_written) *n_written = 0;
+  int rc = check_device_status(h);
+  if (rc) return rc;
+  if (h->sweeps - h->obs_read > (uint64_t)OBS_CAP) h->obs_read = h->sweeps - OBS_CAP;
+  const int64_t avail = (int64_t)(h->sweeps - h->obs_read);
+  const int64_t cnt = std::min<int64_t>(avail, max_sweeps);
+  const int row = h->q + 1;
+  int64_t done = 0;
+  while (done < cnt) {
+    const int64_t slot = (int64_t)((h->obs_read + done) % OBS_CAP);
+    const int64_t run = std::min<int64_t>(cnt - done, OBS_CAP - slot);
+    CK(cudaMemcpy(out + done * row, h->obs + slot * row, run * row * 8, cudaMemcpyDeviceToHost));
+    done += run;
+  }
+  h->obs_read += cnt;
+  if (n_written) *n_written = (int)cnt;
+  return SW_OK;
+}
+
+int sw_get_spins(sw_handle* h, int8_t* dst, int is_device) {
+  if (!h || !dst) return fail(SW_ERR_ARG, "sw_get_spins: bad arguments");
+  int rc = check_device_status(h);
+  if (rc) return rc;
+  CK(cudaMemcpy(dst, h->spins, (int64_t)h->L * h->L,
+                is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
+  return SW_OK;
+}
+
+int sw_set_spins(sw_handle* h, const int8_t* src, int is_device) {
+  if (!h || !src) return fail(SW_ERR_ARG, "sw_set_spins: bad arguments");
+  const int64_t N = (int64_t)h->L * h->L;
+  // Host input is staged in the label buffer (4N bytes, rewritten by the
+  // next sweep) and validated there by a kernel; device input is validated
+  // in place.  The spins change only if every value is in [0, q).
+  const int8_t* dsrc = src;
+  if (!is_device) {
+    int8_t* staging = reinterpret_cast<int8_t*>(h->labels);
+    CK(cudaMemcpyAsync(staging, src, N, cudaMemcpyHostToDevice, h->stream));
+    dsrc = staging;
+    h->dump_valid = false;
+  }
+  CK(cudaMemsetAsync(h->chk, 0, sizeof(int), h->stream));
+  CK(launch_check_spins(dsrc, N, h->q, h->chk, h->stream));
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, h->chk, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (bad) return fail(SW_ERR_ARG, "sw_set_spins: spin value outside [0, q)");
+  CK(cudaMemcpyAsync(h->spins, dsrc, N, cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return SW_OK;
+}
+
+int sw_debug_dump(sw_handle* h, uint8_t* mask_out, int32_t* labels_out, int is_device) {
+  if (!h) return fail(SW_ERR_ARG, "sw_debug_dump: null handle");
+  if (!h->dump_valid)
+    return fail(SW_ERR_STATE, "sw_debug_dump: no sweep has run since creation or the last sw_set_spins");
+  const int64_t N = (int64_t)h->L * h->L;
+  const cudaMemcpyKind kind = is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (labels_out) {
+    // after a sweep every label points at its tile root and the tile root at
+    // the final root; one pointer jump makes every label canonical
+    CK(launch_site_compress(h->labels, N, h->stream));
+  }
+  int rc = check_device_status(h);
+  if (rc) return rc;
+  if (mask_out) CK(cudaMemcpy(mask_out, h->mask, (N + 3) / 4, kind));
+  if (labels_out) CK(cudaMemcpy(labels_out, h->labels, N * 4, kind));
+  return SW_OK;
+}
+
+int sw_get_info(sw_handle* h, int64_t* info) {
+  if (!h || !info) return fail(SW_ERR_ARG, "sw_get_info: bad arguments");
+  info[0] = h->L;
+  info[1] = h->q;
+  info[2] = (int64_t)h->T;
+  info[3] = (int64_t)h->seed;
+  info[4] = (int64_t)h->sweeps;
+  info[5] = OBS_CAP;
+  info[6] = TILE_H;
+  info[7] = TILE_W;
+  return SW_OK;
+}
+
+void* sw_stream(sw_handle* h) { return h ? (void*)h->stream : nullptr; }
+
+int sw_set_timing(sw_handle* h, int enable) {
+  if (!h) return fail(SW_ERR_ARG, "sw_set_timing: null handle");
+  h->timing = enable != 0;
+  return SW_OK;
+}
+
+int sw_phase_times(sw_handle* h, double* ms, int64_t* n_sweeps) {
+  if (!h || !ms) return fail(SW_ERR_ARG, "sw_phase_times: bad arguments");
+  CK(cudaStreamSynchronize(h->stream));
+  for (int p = 0; p < SW_N_PHASES; ++p) ms[p] = 0.0;
+  const size_t per = SW_N_PHASES + 1;
+  const int64_t n = (int64_t)(h->ev_pending.size() / per);
+  for (int64_t k = 0; k < n; ++k) {
+    for (int p = 0; p < SW_N_PHASES; ++p) {
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, h->ev_pending[k * per + p], h->ev_pending[k * per + p + 1]));
+      ms[p] += t;
+    }
+  }
+  for (auto e : h->ev_pending) h->ev_free.push_back(e);
+  h->ev_pending.clear();
+  if (n_sweeps) *n_sweeps = n;
+  return SW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Stand-alone labeling
+// ---------------------------------------------------------------------------
+namespace {
+int ccl_validate(const void* mask, const void* labels, int H, int W) {
+  if (!mask || !labels) return fail(SW_ERR_ARG, "ccl: null device pointer");
+  if (H < 1 || W < 1 || (int64_t)H * W >= ((int64_t)1 << 31))
+    return fail(SW_ERR_ARG, "ccl: need H, W >= 1 and H*W < 2^31");
+  return SW_OK;
+}
+
+int* ccl_status_ptr() {
+  static int* ptrs[64] = {nullptr};
+  static std::mutex mu;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!ptrs[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_ccl_status) != cudaSuccess) return nullptr;
+    ptrs[dev] = static_cast<int*>(p);
+  }
+  return ptrs[dev];
+}
+}  // namespace
+
+int64_t ccl_workspace_bytes(int H, int W) {
+  if (H < 1 || W < 1 || (int64_t)H * W >= ((int64_t)1 << 31)) return -1;
+  return label_scratch_bytes(make_grid(H, W, 0));
+}
+
+int ccl_label_ws(const uint8_t* bond_mask, int32_t* labels, int H, int W, int periodic,
+                 void* workspace, int64_t ws_bytes, void* stream) {
+  int rc = ccl_validate(bond_mask, labels, H, W);
+  if (rc) return rc;
+  const Grid g = make_grid(H, W, periodic);
+  if (!workspace || ws_bytes < label_scratch_bytes(g) || ((uintptr_t)workspace & 255))
+    return fail(SW_ERR_ARG, "ccl_label_ws: workspace missing, too small or not 256-byte aligned");
+  int* status = ccl_status_ptr();
+  if (!status) return fail(SW_ERR_CUDA, "ccl: cannot resolve the device status word");
+  const LabelScratch s = carve_label_scratch(g, workspace, status);
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CK(launch_tile_label(bond_mask, labels, g, s, st));
+  CK(launch_merge(labels, g, s, st));
+  CK(launch_root_compress(labels, g, s, nullptr, 0, 0, nullptr, st));
+  CK(launch_site_compress(labels, g.n_sites(), st));
+  return SW_OK;
+}
+
+int ccl_label(const uint8_t* bond_mask, int32_t* labels, int H, int W, int periodic, void* stream) {
+  int rc = ccl_validate(bond_mask, labels, H, W);
+  if (rc) return rc;
+  const int64_t bytes = ccl_workspace_bytes(H, W);
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  void* ws = nullptr;
+  cudaError_t e = cudaMallocAsync(&ws, bytes, st);
+  if (e == cudaErrorMemoryAllocation) return fail(SW_ERR_OOM, "ccl_label: out of device memory for scratch");
+  if (e) return cuda_fail(e, "cudaMallocAsync");
+  rc = ccl_label_ws(bond_mask, labels, H, W, periodic, ws, bytes, stream);
+  cudaError_t e2 = cudaFreeAsync(ws, st);
+  if (rc) return rc;
+  if (e2) return cuda_fail(e2, "cudaFreeAsync");
+  return SW_OK;
+}
+
+int ccl_bonds_from_pixels(const uint8_t* px, uint8_t* mask, int H, int W, int periodic, void* stream) {
+  int rc = ccl_validate(px, mask, H, W);
+  if (rc) return rc;
+  CK(launch_pixel_bonds(px, mask, H, W, periodic, static_cast<cudaStream_t>(stream)));
+  return SW_OK;
+}
+
+int ccl_perc_mask(uint64_t k, uint8_t* mask, int H, int W, void* stream) {
+  int rc = ccl_validate(mask, mask, H, W);
+  if (rc) return rc;
+  CK(launch_perc_mask(mask, H, W, k, static_cast<cudaStream_t>(stream)));
+  return SW_OK;
+}
+
+int ccl_status(void) {
+  CK(cudaDeviceSynchronize());
+  int* p = ccl_status_ptr();
+  if (!p) return fail(SW_ERR_CUDA, "ccl_status: cannot resolve the device status word");
+  int v = 0;
+  CK(cudaMemcpy(&v, p, sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaMemset(p, 0, sizeof(int)));
+  if (v) return fail(v, "ccl: a device-side consistency check failed");
+  return SW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,129 @@
+// swccl_device.cuh -- device helpers shared by the sm_103a kernels of libswccl.
+//
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), the packed 2-bit bond
+// mask, and lock-free union-find on shared and global memory.  The union
+// rule hooks the larger root under the smaller one, so every tree's root is
+// the minimum index in it; with labels initialised to their own index this
+// makes the final root of a cluster its minimum site index, the canonical
+// label that breadth-first search seeded in site order produces (Sec. II.B.1).
+#pragma once
+#include <cstdint>
+
+#include "swccl_shared.h"
+
+namespace swccl {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10.  Each round takes the two 32x32->64 products of the even
+// counter words with the published multipliers; the high halves are mixed
+// with the odd words and the round key, the key advances by the Weyl
+// constants between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox(uint4 ctr, uint32_t key_lo, uint32_t key_hi) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    const unsigned long long pa = (unsigned long long)ctr.x * 0xD2511F53ull;
+    const unsigned long long pb = (unsigned long long)ctr.z * 0xCD9E8D57ull;
+    uint4 nxt;
+    nxt.x = (uint32_t)(pb >> 32) ^ ctr.y ^ key_lo;
+    nxt.y = (uint32_t)pb;
+    nxt.z = (uint32_t)(pa >> 32) ^ ctr.w ^ key_hi;
+    nxt.w = (uint32_t)pa;
+    ctr = nxt;
+    key_lo += 0x9E3779B9u;
+    key_hi += 0xBB67AE85u;
+  }
+  return ctr;
+}
+
+__device__ __forceinline__ uint4 draw(uint32_t c0, uint64_t sweep, uint32_t tag, uint64_t seed) {
+  return philox(make_uint4(c0, (uint32_t)sweep, (uint32_t)(sweep >> 32), tag), (uint32_t)seed,
+                (uint32_t)(seed >> 32));
+}
+
+// New state of a cluster from a 32-bit word: floor(w q / 2^32).
+__device__ __forceinline__ int state_of(uint32_t w, int q) {
+  return (int)(((unsigned long long)w * (unsigned)q) >> 32);
+}
+
+// Two bits of site i in the packed mask: bit 0 east bond, bit 1 north bond.
+__device__ __forceinline__ uint32_t site_bits(const uint8_t* mask, int64_t i) {
+  return (uint32_t)(mask[i >> 2] >> (2 * (i & 3))) & 3u;
+}
+
+// Record a device-side failure without trapping: the first code wins.
+__device__ __forceinline__ void set_error(int* err, int code) {
+  if (err) atomicCAS(err, 0, code);
+}
+
+// ---------------------------------------------------------------------------
+// Union-find in shared memory.  par[x] <= x always; roots satisfy par[r] == r.
+// ---------------------------------------------------------------------------
+// Walks at most `limit` steps (a tree of the tile has fewer nodes); on
+// overrun the error word is set and the walk stops.
+__device__ __forceinline__ int sm_find(volatile int* par, int x, int limit, int* err) {
+  int p = par[x];
+  int steps = 0;
+  while (p != x) {
+    const int gp = par[p];
+    if (gp != p) par[x] = gp;   // path halving: point x at its grandparent
+    x = p;
+    p = gp;
+    if (++steps > limit) { set_error(err, SW_ERR_STATE); return x; }
+  }
+  return x;
+}
+
+// Join the sets of a and b.  atomicMin hooks the larger root under the
+// smaller; when the target was hooked meanwhile, the returned old parent is
+// joined in the next round, so no link is lost.  Every round strictly lowers
+// the larger operand, so at most `limit` rounds run.
+__device__ __forceinline__ void sm_union(int* par, int a, int b, int limit, int* err) {
+  volatile int* vp = par;
+  for (int rounds = 0; rounds <= limit; ++rounds) {
+    a = sm_find(vp, a, limit, err);
+    b = sm_find(vp, b, limit, err);
+    if (a == b) return;
+    if (a > b) { const int t = a; a = b; b = t; }
+    const int old = atomicMin(&par[b], a);
+    if (old == b) return;
+    b = old;
+  }
+  set_error(err, SW_ERR_STATE);
+}
+
+// ---------------------------------------------------------------------------
+// Union-find on a global int32 array (the label array itself: the entry of a
+// tile root is its parent pointer).  Loads bypass L1 (ld.cg) because other
+// SMs update the array during the merge.  Bounded by `limit` steps: on
+// overrun the error word is set and the walk stops.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int g_load(const int* p) { return __ldcg(p); }
+
+__device__ __forceinline__ int g_find(int* lab, int x, int limit, int* err) {
+  int p = g_load(lab + x);
+  int steps = 0;
+  while (p != x) {
+    const int gp = g_load(lab + p);
+    if (gp != p) lab[x] = gp;
+    x = p;
+    p = gp;
+    if (++steps > limit) { set_error(err, SW_ERR_STATE); return x; }
+  }
+  return x;
+}
+
+__device__ __forceinline__ void g_union(int* lab, int a, int b, int limit, int* err) {
+  for (int rounds = 0; rounds <= limit; ++rounds) {
+    a = g_find(lab, a, limit, err);
+    b = g_find(lab, b, limit, err);
+    if (a == b) return;
+    if (a > b) { const int t = a; a = b; b = t; }
+    const int old = atomicMin(lab + b, a);
+    if (old == b) return;
+    b = old;
+  }
+  set_error(err, SW_ERR_STATE);
+}
+
+}  // namespace swccl

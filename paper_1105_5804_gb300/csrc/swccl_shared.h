@@ -1,0 +1,99 @@
+// swccl_shared.h -- declarations shared by the host driver and the kernel
+// translation units of libswccl (not part of the public ABI).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/swccl.h"
+
+namespace swccl {
+
+// Philox tags (counter word 3).
+enum : uint32_t { TAG_BOND = 0, TAG_FLIP = 1, TAG_INIT = 2, TAG_PERC = 3 };
+
+// Tile of the local labeling phase: TILE_H rows x TILE_W columns, one CTA
+// of LABEL_THREADS threads per tile.  TILE_W and TILE_H are multiples of 32;
+// TILE_W is a power of two.
+constexpr int TILE_H = 64;
+constexpr int TILE_W = 128;
+constexpr int TILE_W_LOG2 = 7;
+constexpr int LABEL_THREADS = 512;
+
+// Per-tile seam record written by the local labeling phase and read by the
+// merge: labels of the four tile edges and the raw bond bits leaving the
+// tile.  Labels are global site indices of tile-local roots.
+struct SeamLayout {
+  static constexpr int COL_L = 0;                       // int32[TILE_H]: column 0
+  static constexpr int COL_R = COL_L + TILE_H;          // int32[TILE_H]: column w-1
+  static constexpr int ROW_B = COL_R + TILE_H;          // int32[TILE_W]: row 0
+  static constexpr int ROW_T = ROW_B + TILE_W;          // int32[TILE_W]: row h-1
+  static constexpr int E_BITS = ROW_T + TILE_W;         // uint32[TILE_H/32]: east bits of column w-1
+  static constexpr int N_BITS = E_BITS + TILE_H / 32;   // uint32[TILE_W/32]: north bits of row h-1
+  static constexpr int INTS = N_BITS + TILE_W / 32;
+};
+
+// Geometry of one labeling problem (an H x W grid cut into tiles).
+struct Grid {
+  int H, W;
+  int tiles_x, tiles_y;
+  int periodic;
+  __host__ __device__ int64_t n_sites() const { return (int64_t)H * W; }
+  __host__ __device__ int n_tiles() const { return tiles_x * tiles_y; }
+};
+
+inline Grid make_grid(int H, int W, int periodic) {
+  Grid g;
+  g.H = H;
+  g.W = W;
+  g.tiles_x = (W + TILE_W - 1) / TILE_W;
+  g.tiles_y = (H + TILE_H - 1) / TILE_H;
+  g.periodic = periodic ? 1 : 0;
+  return g;
+}
+
+// Scratch of one labeling problem.
+struct LabelScratch {
+  int32_t* roots;        // n_tiles * TILE_H * TILE_W: tile-root lists
+  int32_t* root_counts;  // n_tiles
+  int32_t* seams;        // n_tiles * SeamLayout::INTS
+  int* err;              // device status word
+};
+
+// Control block of a Swendsen-Wang chain, in device memory.
+struct SwCtl {
+  unsigned long long sweep;  // index of the sweep being computed
+  int err;                   // first device-side failure (SW_ERR_*)
+  int pad;
+};
+
+// Bytes of LabelScratch for a grid (each part 256-byte aligned).
+int64_t label_scratch_bytes(const Grid& g);
+LabelScratch carve_label_scratch(const Grid& g, void* base, int* err);
+
+// ---------------------------------------------------------------------------
+// Launchers (each enqueues on `st`, returns the launch error).
+// ---------------------------------------------------------------------------
+cudaError_t launch_init_spins(int8_t* spins, int L, int q, uint64_t seed, int hot, cudaStream_t st);
+cudaError_t launch_activate(const int8_t* spins, uint8_t* mask, int L, uint64_t T, uint64_t seed,
+                            const SwCtl* ctl, int64_t* obs_ring, int obs_cap, int q,
+                            cudaStream_t st);
+cudaError_t launch_perc_mask(uint8_t* mask, int H, int W, uint64_t k, cudaStream_t st);
+cudaError_t launch_pixel_bonds(const uint8_t* px, uint8_t* mask, int H, int W, int periodic,
+                               cudaStream_t st);
+cudaError_t launch_check_spins(const int8_t* spins, int64_t n, int q, int* err, cudaStream_t st);
+
+cudaError_t launch_tile_label(const uint8_t* mask, int32_t* labels, const Grid& g,
+                              const LabelScratch& s, cudaStream_t st);
+cudaError_t launch_merge(int32_t* labels, const Grid& g, const LabelScratch& s, cudaStream_t st);
+// Root compression; when `spins` is non-null also draws each final root's
+// new state (FLIP tag, sweep from ctl) into spins[root].
+cudaError_t launch_root_compress(int32_t* labels, const Grid& g, const LabelScratch& s,
+                                 int8_t* spins, int q, uint64_t seed, const SwCtl* ctl,
+                                 cudaStream_t st);
+cudaError_t launch_site_compress(int32_t* labels, int64_t n_sites, cudaStream_t st);
+
+cudaError_t launch_flip(int8_t* spins, const int32_t* labels, int L, int q, const SwCtl* ctl,
+                        int64_t* obs_ring, int obs_cap, cudaStream_t st);
+cudaError_t launch_advance(SwCtl* ctl, cudaStream_t st);
+
+}  // namespace swccl

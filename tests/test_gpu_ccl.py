@@ -1,0 +1,148 @@
+"""GPU parity of the stand-alone labeling path against the oracle, through the C ABI.
+
+Masks: critical percolation (generated on the GPU by ccl_perc_mask and
+compared bit for bit with the oracle's), numpy random masks at several
+densities, image bonds.  Shapes span one tile, several tiles, ragged tails
+in both directions, single rows and columns, periodic and open boundaries.
+Labels must equal the oracle's breadth-first-search labels element by
+element (integer work: bit-exact).  At the 4096^2 size of the labeling
+workload, seeds 0..9 are compared in full and all 100 seeds are checked for
+the properties every canonical labeling has.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1105_5804_gb300 as sw
+from paper_1105_5804_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(1, 1), (1, 7), (7, 1), (2, 2), (3, 5), (64, 128), (65, 129), (63, 127), (128, 256),
+          (200, 300), (1, 1000), (1000, 1), (130, 4), (4, 130), (257, 129), (513, 385)]
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _gpu_label(mask_np, H, W, periodic):
+    m = _dev(mask_np)
+    lab = torch.full((H * W,), -7, dtype=torch.int32, device="cuda")
+    sw.ccl_label(m, lab, H, W, periodic)
+    sw.ccl_status()
+    return lab.cpu().numpy()
+
+
+@pytest.mark.parametrize("H,W", SHAPES)
+def test_perc_mask_bit_exact(H, W):
+    m = torch.zeros(sw.mask_bytes(H * W), dtype=torch.uint8, device="cuda")
+    for k in (0, 3, 2 ** 40 + 5):
+        sw.ccl_perc_mask(k, m, H, W)
+        assert np.array_equal(m.cpu().numpy(), oracle.perc_mask(H, W, k))
+
+
+@pytest.mark.parametrize("H,W", SHAPES)
+@pytest.mark.parametrize("periodic", [True, False])
+@pytest.mark.parametrize("p", [0.25, 0.5, 0.62, 0.9, 1.0])
+def test_labels_random_masks(H, W, periodic, p):
+    mask = inputs.random_mask(H, W, p, seed=H * 7919 + W * 31 + int(100 * p))
+    ref, _ = oracle.label(mask, H, W, periodic)
+    assert np.array_equal(_gpu_label(mask, H, W, periodic), ref)
+
+
+def test_labels_empty_and_full_masks():
+    for H, W in [(64, 128), (100, 300), (5, 5)]:
+        for periodic in (True, False):
+            for fill in (0x00, 0xFF):
+                mask = np.full(sw.mask_bytes(H * W), fill, dtype=np.uint8)
+                ref, _ = oracle.label(mask, H, W, periodic)
+                assert np.array_equal(_gpu_label(mask, H, W, periodic), ref)
+
+
+def test_labels_long_snakes_cross_many_tiles():
+    """A single path that winds through every row of a multi-tile grid: the
+    worst case for tile merging (one cluster, many hooks)."""
+    H, W = 300, 260
+    east = np.zeros((H, W), dtype=np.uint8)
+    north = np.zeros((H, W), dtype=np.uint8)
+    east[:, :-1] = 1
+    for y in range(H - 1):
+        north[y, W - 1 if y % 2 == 0 else 0] = 1
+    mask = oracle.pack_mask(east.reshape(-1), north.reshape(-1))
+    for periodic in (True, False):
+        ref, n = oracle.label(mask, H, W, periodic)
+        assert n == 1
+        assert np.array_equal(_gpu_label(mask, H, W, periodic), ref)
+
+
+@pytest.mark.parametrize("H,W", [(64, 128), (200, 300), (513, 385), (1000, 999)])
+@pytest.mark.parametrize("periodic", [True, False])
+def test_labels_perc_and_image_masks(H, W, periodic):
+    for k in (1, 2):
+        mask = oracle.perc_mask(H, W, k)
+        ref, _ = oracle.label(mask, H, W, periodic)
+        assert np.array_equal(_gpu_label(mask, H, W, periodic), ref)
+    px = inputs.blurred_noise_image(H, W, seed=H + W)
+    m = torch.zeros(sw.mask_bytes(H * W), dtype=torch.uint8, device="cuda")
+    sw.ccl_bonds_from_pixels(_dev(px.reshape(-1)), m, H, W, periodic)
+    om = oracle.bonds_from_pixels(px, periodic)
+    assert np.array_equal(m.cpu().numpy(), om)
+    ref, _ = oracle.label(om, H, W, periodic)
+    assert np.array_equal(_gpu_label(om, H, W, periodic), ref)
+
+
+def test_label_ws_matches_label_and_reuses_workspace():
+    H, W = 777, 555
+    ws = torch.empty(sw.ccl_workspace_bytes(H, W), dtype=torch.uint8, device="cuda")
+    for k in range(3):
+        mask = oracle.perc_mask(H, W, 10 + k)
+        ref, _ = oracle.label(mask, H, W, True)
+        lab = torch.empty(H * W, dtype=torch.int32, device="cuda")
+        sw.ccl_label_ws(_dev(mask), lab, H, W, True, ws)
+        sw.ccl_status()
+        assert np.array_equal(lab.cpu().numpy(), ref)
+
+
+def _invariants(lab, mask, H, W):
+    """Properties of a canonical labeling that hold at any size (torch on GPU)."""
+    N = H * W
+    i = torch.arange(N, device="cuda", dtype=torch.int64)
+    l64 = lab.long()
+    assert bool((l64 <= i).all())
+    assert bool((l64 >= 0).all())
+    assert torch.equal(lab[l64], lab)
+    m = mask.long()
+    bits = (m[i >> 2] >> (2 * (i & 3))) & 3
+    y, x = i // W, i % W
+    e = (bits & 1).bool()
+    n = (bits & 2).bool()
+    east = y * W + (x + 1) % W
+    north = ((y + 1) % H) * W + x
+    assert torch.equal(lab[e], lab[east[e]])
+    assert torch.equal(lab[n], lab[north[n]])
+    return int((l64 == i).sum())
+
+
+def test_labeling_workload_4096_seeds():
+    """Critical percolation on the periodic 4096 x 4096 lattice, seeds 0..99:
+    seeds 0..9 element by element against the oracle, every seed for the
+    invariants and a cluster density near (3 sqrt3 - 5)/2."""
+    H = W = 4096
+    mask = torch.empty(sw.mask_bytes(H * W), dtype=torch.uint8, device="cuda")
+    lab = torch.empty(H * W, dtype=torch.int32, device="cuda")
+    dens = []
+    for k in range(100):
+        sw.ccl_perc_mask(k, mask, H, W)
+        sw.ccl_label(mask, lab, H, W, True)
+        sw.ccl_status()
+        if k < 10:
+            om = oracle.perc_mask(H, W, k)
+            assert np.array_equal(mask.cpu().numpy(), om)
+            ref, n = oracle.label(om, H, W, True)
+            assert np.array_equal(lab.cpu().numpy(), ref)
+        n_roots = _invariants(lab, mask, H, W)
+        dens.append(n_roots / (H * W))
+    import oracle.exact as ex
+    assert abs(np.mean(dens) - ex.PERC_CLUSTER_DENSITY) < 2e-4

@@ -1,0 +1,196 @@
+"""GPU parity of the Swendsen-Wang chain against the oracle, through the C ABI.
+
+Every sweep compares the bond mask, the canonical labels, the new spins and
+the observables bit for bit (integer work).  Cases: the L = 64 Ising chain
+at beta_c from a cold start with seed 1 for 1000 sweeps; odd lattice sizes
+that leave ragged tiles (L = 4, 8, 36, 100, 132, 196); q = 2, 3, 4, 5, 9
+and 127 (register and shared-memory state counters); the degenerate
+thresholds T = 0 (no bond opens) and T = 2^32 (every equal bond opens); hot
+starts.  At L = 16384, the size the benchmark times, sampled sweeps are
+checked by one-step equivalence: the oracle steps the GPU's pre-sweep spins
+once and must reproduce the GPU's mask, labels, spins and observables.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1105_5804_gb300 as sw
+
+pytestmark = pytest.mark.gpu
+
+KC = 0.5 * math.log(1.0 + math.sqrt(2.0))
+
+
+def _run_parity(L, q, T, seed, hot, n_sweeps, sweep_graph=True):
+    h = sw.sw_create_threshold(L, q, T, seed, hot)
+    try:
+        if not sweep_graph:
+            sw.sw_set_timing(h, True)
+        s = oracle.init_spins(L, q, seed, hot)
+        assert np.array_equal(sw.sw_get_spins(h), s)
+        for k in range(n_sweeps):
+            sw.sw_sweep(h, 1)
+            s, m, lab, obs = oracle.sweep(L, q, T, seed, k, s)
+            gm, glab = sw.sw_debug_dump(h)
+            assert np.array_equal(gm, m), ("mask", L, q, k)
+            assert np.array_equal(glab, lab), ("labels", L, q, k)
+            assert np.array_equal(sw.sw_get_spins(h), s), ("spins", L, q, k)
+            gobs = sw.sw_observables(h, 4)
+            assert gobs.shape[0] == 1 and np.array_equal(gobs[0], obs), ("obs", L, q, k)
+    finally:
+        sw.sw_destroy(h)
+
+
+def test_ising_L64_cold_start_1000_sweeps_bit_exact():
+    """The small chain configuration: L = 64, q = 2, beta_c (Ising), cold
+    start, seed 1, 1000 sweeps, every sweep compared; then <E>, <|M|> of the
+    chain equal the oracle's (identical sequences)."""
+    L, q, seed = 64, 2, 1
+    T = oracle.threshold(oracle.coupling_K(q, KC, 1.0, oracle.CONV_ISING))
+    h = sw.sw_create_ex(L, q, KC, 1.0, sw.SW_CONV_ISING, seed, False)
+    try:
+        s = oracle.init_spins(L, q, seed, False)
+        gobs_all = []
+        for k in range(1000):
+            sw.sw_sweep(h, 1)
+            s, m, lab, obs = oracle.sweep(L, q, T, seed, k, s)
+            gm, glab = sw.sw_debug_dump(h)
+            assert np.array_equal(gm, m), k
+            assert np.array_equal(glab, lab), k
+            assert np.array_equal(sw.sw_get_spins(h), s), k
+            g = sw.sw_observables(h, 4)
+            assert np.array_equal(g[0], obs), k
+            gobs_all.append(g[0])
+        gobs_all = np.array(gobs_all)
+        _, oobs = oracle.chain(L, q, T, seed, 0, 1000, oracle.init_spins(L, q, seed, False))
+        assert np.array_equal(gobs_all, oobs)
+        N = L * L
+        E = -(2 * gobs_all[:, 0] - 2 * N) / N
+        M = np.abs(gobs_all[:, 1] - gobs_all[:, 2]) / N
+        assert abs(E[100:].mean() - (-(2 * oobs[100:, 0] - 2 * N) / N).mean()) == 0.0
+        assert 1.30 < -E[100:].mean() < 1.55 and 0.3 < M[100:].mean() < 0.95
+    finally:
+        sw.sw_destroy(h)
+
+
+@pytest.mark.parametrize("L", [4, 8, 36, 100, 132, 196])
+@pytest.mark.parametrize("q", [2, 3, 4])
+def test_small_lattices_hot_start(L, q):
+    beta = math.log(1 + math.sqrt(q))                 # Potts beta_c
+    T = oracle.threshold(oracle.coupling_K(q, beta, 1.0, oracle.CONV_POTTS))
+    _run_parity(L, q, T, seed=1000 + L + q, hot=True, n_sweeps=12)
+
+
+@pytest.mark.parametrize("q", [5, 9, 127])
+def test_many_states(q):
+    T = oracle.threshold(oracle.coupling_K(q, math.log(1 + math.sqrt(q)), 1.0, oracle.CONV_POTTS))
+    _run_parity(132, q, T, seed=7, hot=True, n_sweeps=6)
+
+
+@pytest.mark.parametrize("T", [0, 1, 1 << 31, (1 << 32) - 1, 1 << 32])
+def test_degenerate_thresholds(T):
+    _run_parity(68, 2, T, seed=3, hot=True, n_sweeps=4)
+
+
+def test_timed_mode_is_the_same_chain():
+    T = oracle.threshold(oracle.coupling_K(2, KC, 1.0, oracle.CONV_ISING))
+    _run_parity(100, 2, T, seed=11, hot=True, n_sweeps=5, sweep_graph=False)
+
+
+def test_many_sweeps_per_call_and_observable_ring():
+    L, q, seed = 36, 3, 5
+    T = oracle.threshold(oracle.coupling_K(q, math.log(1 + math.sqrt(3)), 1.0, oracle.CONV_POTTS))
+    h = sw.sw_create_threshold(L, q, T, seed, True)
+    try:
+        sw.sw_sweep(h, 300)
+        s, obs = oracle.chain(L, q, T, seed, 0, 300, oracle.init_spins(L, q, seed, True))
+        assert np.array_equal(sw.sw_observables(h, 1000), obs)
+        assert np.array_equal(sw.sw_get_spins(h), s)
+        # ring of 4096: after 5000 more sweeps only the last 4096 remain
+        sw.sw_sweep(h, 5000)
+        s2, obs2 = oracle.chain(L, q, T, seed, 300, 5000, s)
+        got = sw.sw_observables(h, 8000)
+        assert got.shape[0] == 4096 and np.array_equal(got, obs2[-4096:])
+        assert sw.sw_get_info(h)["sweeps"] == 5300
+    finally:
+        sw.sw_destroy(h)
+
+
+def test_set_spins_and_errors():
+    L, q = 64, 3
+    h = sw.sw_create_threshold(L, q, 1 << 31, 9, False)
+    try:
+        rng = np.random.default_rng(0)
+        s = rng.integers(0, q, L * L).astype(np.int8)
+        sw.sw_set_spins(h, s)
+        assert np.array_equal(sw.sw_get_spins(h), s)
+        sd = torch.from_numpy(np.roll(s, 5)).cuda()
+        sw.sw_set_spins(h, sd)
+        assert np.array_equal(sw.sw_get_spins(h), np.roll(s, 5))
+        bad = s.copy()
+        bad[17] = q
+        with pytest.raises(sw.SwcclError):
+            sw.sw_set_spins(h, bad)
+        with pytest.raises(sw.SwcclError):
+            sw.sw_set_spins(h, torch.from_numpy(bad).cuda())
+        assert np.array_equal(sw.sw_get_spins(h), np.roll(s, 5))    # unchanged
+        sw.sw_sweep(h, 2)
+        s1, _, _, _ = oracle.sweep(L, q, 1 << 31, 9, 0, np.roll(s, 5))
+        s2, _, _, _ = oracle.sweep(L, q, 1 << 31, 9, 1, s1)
+        assert np.array_equal(sw.sw_get_spins(h), s2)
+        out = torch.empty(L * L, dtype=torch.int8, device="cuda")
+        sw.sw_get_spins(h, out)
+        assert np.array_equal(out.cpu().numpy(), s2)
+    finally:
+        sw.sw_destroy(h)
+
+
+def test_user_stream_and_two_handles_are_independent():
+    st = torch.cuda.Stream()
+    T = oracle.threshold(0.9)
+    a = sw.sw_create_threshold(64, 2, T, 42, True, st)
+    b = sw.sw_create_threshold(64, 2, T, 42, True)
+    try:
+        assert sw.sw_stream(a) == st.cuda_stream
+        sw.sw_sweep(a, 7)
+        sw.sw_sweep(b, 7)
+        assert np.array_equal(sw.sw_get_spins(a), sw.sw_get_spins(b))
+    finally:
+        sw.sw_destroy(a)
+        sw.sw_destroy(b)
+
+
+@pytest.mark.parametrize("q,beta,conv", [(2, KC, sw.SW_CONV_ISING), (4, math.log(3.0), sw.SW_CONV_POTTS)])
+def test_L16384_one_step_equivalence(q, beta, conv):
+    """The benchmark's lattice: L = 16384, hot start seed 7.  Sampled sweeps 0
+    and 2 (q = 2) / 0 (q = 4): the oracle steps the GPU's pre-sweep spins once
+    and must reproduce the GPU's mask, labels, spins and observables."""
+    L, seed = 16384, 7
+    T = oracle.threshold(oracle.coupling_K(q, beta, 1.0, conv))
+    h = sw.sw_create_ex(L, q, beta, 1.0, conv, seed, True)
+    try:
+        s = sw.sw_get_spins(h)
+        assert np.array_equal(s[:1 << 16], oracle.init_spins(L, q, seed, True)[:1 << 16])
+        samples = (0, 2) if q == 2 else (0,)
+        done = 0
+        for k in samples:
+            if k > done:
+                sw.sw_sweep(h, k - done)
+                sw.sw_observables(h, 4096)
+                s = sw.sw_get_spins(h)
+            sw.sw_sweep(h, 1)
+            done = k + 1
+            gm, glab = sw.sw_debug_dump(h)
+            gs = sw.sw_get_spins(h)
+            gobs = sw.sw_observables(h, 4)
+            s_new, m, lab, obs = oracle.sweep(L, q, T, seed, k, s)
+            assert np.array_equal(gm, m)
+            assert np.array_equal(glab, lab)
+            assert np.array_equal(gs, s_new)
+            assert np.array_equal(gobs[-1], obs)
+            s = gs
+    finally:
+        sw.sw_destroy(h)
