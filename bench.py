@@ -216,7 +216,7 @@ def run_ours(args):
     import paper_1105_5804_gb300 as sw
     sw.lib()    # fails loudly when the extension is missing
 
-    L, q = L_BENCH, Q_BENCH
+    L, q = args.L, Q_BENCH
     N = L * L
     seed = SEED_BENCH + rank
     h = sw.sw_create_ex(L, q, KC_ISING, 1.0, sw.SW_CONV_ISING, seed, True)
@@ -265,7 +265,7 @@ def run_ours(args):
 
     # end to end through the C ABI with host buffers: upload spins, one sweep,
     # read observables and spins back, every step
-    e2e_steps = max(3, min(args.steps, 20))
+    e2e_steps = 0 if args.no_e2e else max(3, min(args.steps, 20))
     host_in = torch.empty(N, dtype=torch.int8).pin_memory()
     host_out = torch.empty(N, dtype=torch.int8).pin_memory()
     sw.sw_get_spins(h, host_in.numpy())    # warm the copies
@@ -282,7 +282,7 @@ def run_ours(args):
         t = torch.tensor([te], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         te = float(t.item())
-    e2e_value = world * N * e2e_steps / (te * 1e9)
+    e2e_value = world * N * e2e_steps / (te * 1e9) if e2e_steps else None
 
     secondary = {}
     if rank == 0 and not args.no_secondary:
@@ -345,6 +345,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--L", type=int, default=L_BENCH,
+                    help="lattice size (profiling of smaller cases only; the benchmark is L=16384)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -114,7 +114,7 @@ k_tile_label(const uint8_t* __restrict__ mask, int32_t* __restrict__ labels, Gri
     int r = sidx, gr = 0;
     if (inside) {
       r = sm_find(par, sidx, TILE_SITES, s.err);
-      par[sidx] = r;
+      atomicMin(&par[sidx], r);
       gr = (y0 + (r >> TILE_W_LOG2)) * W + x0 + (r & (TILE_W - 1));
       labels[(int64_t)(y0 + ly) * W + x0 + lx] = gr;
     }
@@ -228,7 +228,7 @@ k_root_compress(int32_t* __restrict__ labels, Grid g, LabelScratch s, int8_t* __
   for (int k = threadIdx.x; k < n; k += ROOT_THREADS) {
     const int r = list[k];
     const int R = g_find(labels, r, limit, s.err);
-    if (R != r) labels[r] = R;
+    if (R != r) atomicMin(labels + r, R);
     if (spins && R == r) spins[r] = (int8_t)state_of(draw((uint32_t)r, sweep, TAG_FLIP, seed).x, q);
   }
 }

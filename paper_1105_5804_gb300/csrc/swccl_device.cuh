@@ -59,14 +59,18 @@ __device__ __forceinline__ void set_error(int* err, int code) {
 // ---------------------------------------------------------------------------
 // Union-find in shared memory.  par[x] <= x always; roots satisfy par[r] == r.
 // ---------------------------------------------------------------------------
-// Walks at most `limit` steps (a tree of the tile has fewer nodes); on
-// overrun the error word is set and the walk stops.
+// Path halving writes with atomicMin, never with a plain store: a plain
+// store of a grandparent read earlier could overwrite a smaller pointer that
+// another thread has written since (for instance the final root), undoing
+// its compression.  With atomicMin every entry only ever decreases, and a
+// root, the minimum of its tree, once written stays.  Walks at most `limit`
+// steps (a tile tree has fewer nodes); on overrun the error word is set.
 __device__ __forceinline__ int sm_find(volatile int* par, int x, int limit, int* err) {
   int p = par[x];
   int steps = 0;
   while (p != x) {
     const int gp = par[p];
-    if (gp != p) par[x] = gp;   // path halving: point x at its grandparent
+    if (gp != p) atomicMin((int*)&par[x], gp);   // path halving
     x = p;
     p = gp;
     if (++steps > limit) { set_error(err, SW_ERR_STATE); return x; }
@@ -105,7 +109,7 @@ __device__ __forceinline__ int g_find(int* lab, int x, int limit, int* err) {
   int steps = 0;
   while (p != x) {
     const int gp = g_load(lab + p);
-    if (gp != p) lab[x] = gp;
+    if (gp != p) atomicMin(lab + x, gp);   // path halving, decreasing only (see sm_find)
     x = p;
     p = gp;
     if (++steps > limit) { set_error(err, SW_ERR_STATE); return x; }

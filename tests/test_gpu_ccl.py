@@ -61,20 +61,42 @@ def test_labels_empty_and_full_masks():
                 assert np.array_equal(_gpu_label(mask, H, W, periodic), ref)
 
 
-def test_labels_long_snakes_cross_many_tiles():
-    """A single path that winds through every row of a multi-tile grid: the
-    worst case for tile merging (one cluster, many hooks)."""
-    H, W = 300, 260
+def _snake(H, W, vertical):
     east = np.zeros((H, W), dtype=np.uint8)
     north = np.zeros((H, W), dtype=np.uint8)
-    east[:, :-1] = 1
-    for y in range(H - 1):
-        north[y, W - 1 if y % 2 == 0 else 0] = 1
-    mask = oracle.pack_mask(east.reshape(-1), north.reshape(-1))
+    if not vertical:
+        east[:, :-1] = 1
+        for y in range(H - 1):
+            north[y, W - 1 if y % 2 == 0 else 0] = 1
+    else:
+        north[:-1, :] = 1
+        for x in range(W - 1):
+            east[H - 1 if x % 2 == 0 else 0, x] = 1
+    return oracle.pack_mask(east.reshape(-1), north.reshape(-1))
+
+
+def _comb(H, W):
+    east = np.zeros((H, W), dtype=np.uint8)
+    north = np.zeros((H, W), dtype=np.uint8)
+    east[H // 2, :-1] = 1           # spine along one row
+    north[:-1, :] = 1               # teeth along every column
+    north[H // 2 - 1, 1::2] = 0     # cut odd teeth below the spine
+    return oracle.pack_mask(east.reshape(-1), north.reshape(-1))
+
+
+@pytest.mark.parametrize("H,W", [(300, 260), (260, 300), (1000, 130), (129, 1025)])
+@pytest.mark.parametrize("kind", ["snake_h", "snake_v", "comb"])
+def test_labels_adversarial_long_paths(H, W, kind):
+    """One path that winds through every row (or column) of a multi-tile
+    grid -- the worst case for seam merging: one cluster, a chain of hooks
+    through every tile -- and a comb whose teeth hang off one spine."""
+    mask = _comb(H, W) if kind == "comb" else _snake(H, W, kind == "snake_v")
     for periodic in (True, False):
         ref, n = oracle.label(mask, H, W, periodic)
-        assert n == 1
-        assert np.array_equal(_gpu_label(mask, H, W, periodic), ref)
+        if kind != "comb":
+            assert n == 1
+        for _ in range(3):          # the merge is racy by design: repeat
+            assert np.array_equal(_gpu_label(mask, H, W, periodic), ref)
 
 
 @pytest.mark.parametrize("H,W", [(64, 128), (200, 300), (513, 385), (1000, 999)])
