@@ -28,24 +28,48 @@
 //                 cluster's new state here (Sec. II.D), keyed by the root.
 //  k_site_compress  label[i] = label[label[i]] for every site (stand-alone
 //                 labeling only: leaves every label canonical).
+#include <climits>
+
 #include "swccl_device.cuh"
 
 namespace swccl {
 
 namespace {
 constexpr int TILE_SITES = TILE_H * TILE_W;
-constexpr int NWARPS = LABEL_THREADS / 32;
-constexpr int SEGS = TILE_W / 32;
 constexpr unsigned FULL = 0xFFFFFFFFu;
 }  // namespace
 
 // Shared-memory bond bits per tile site: bit 0 east bond inside the tile,
 // bit 1 north bond inside the tile, bits 2..3 the raw mask bits.
+__device__ __forceinline__ uint32_t tile_bits(uint32_t m, int lx, int ly, int w, int h) {
+  uint32_t b = m << 2;
+  if ((m & 1u) && lx + 1 < w) b |= 1u;
+  if ((m & 2u) && ly + 1 < h) b |= 2u;
+  return b;
+}
+
+// Local labeling of one tile.
+//  1. the tile's bond bits go to shared memory;
+//  2. warp c sweeps its 32-column strip from row 0 upwards.  The labels of
+//     the row below stay in registers.  A row is cut into runs of
+//     east-joined sites with one ballot; each run takes the smallest label
+//     among the sites below it that reach it by a north bond (a segmented
+//     minimum over the run's lanes, five shuffle steps), or, if none does, a
+//     fresh label: the index of its first site.  Only a run reached from
+//     below by two different labels joins them, with the shared-memory
+//     union-find; every other site is labeled without an atomic.
+//  3. east bonds between strips are joined with the union-find, skipping a
+//     bond whose two ends were already joined through the row below;
+//  4. every site resolves its root; the root is the smallest index of the
+//     tile component (a fresh label is always a run's first site, the
+//     component's smallest site starts a run nothing reaches from below, and
+//     unions hook the larger root under the smaller), so its global index is
+//     the minimum site index of the tile component.
 __global__ void __launch_bounds__(LABEL_THREADS)
 k_tile_label(const uint8_t* __restrict__ mask, int32_t* __restrict__ labels, Grid g,
              LabelScratch s) {
   __shared__ int par[TILE_SITES];
-  __shared__ uint8_t bits[TILE_SITES];
+  __shared__ __align__(16) uint8_t bits[TILE_SITES];
   __shared__ int n_roots;
 
   const int t = blockIdx.x;
@@ -57,52 +81,77 @@ k_tile_label(const uint8_t* __restrict__ mask, int32_t* __restrict__ labels, Gri
   if (threadIdx.x == 0) n_roots = 0;
 
   // 1. bond bits of the tile
-  for (int sidx = threadIdx.x; sidx < TILE_SITES; sidx += LABEL_THREADS) {
-    const int ly = sidx >> TILE_W_LOG2, lx = sidx & (TILE_W - 1);
-    uint32_t b = 0;
-    if (ly < h && lx < w) {
-      const uint32_t m = site_bits(mask, (int64_t)(y0 + ly) * W + x0 + lx);
-      b = m << 2;
-      if ((m & 1u) && lx + 1 < w) b |= 1u;
-      if ((m & 2u) && ly + 1 < h) b |= 2u;
-    }
-    bits[sidx] = (uint8_t)b;
-  }
-  __syncthreads();
-
-  // 2. row runs: one warp per row, 32 sites per ballot, a carry joins segments
-  for (int ly = warp; ly < TILE_H; ly += NWARPS) {
-    int carry = -1;
+  if ((W & 3) == 0) {
+    // rows start on mask-byte boundaries: one byte = four sites per thread
+    constexpr int BPR = TILE_W / 4;
+    for (int k = threadIdx.x; k < BPR * TILE_H; k += LABEL_THREADS) {
+      const int ly = k / BPR, lx0 = (k - ly * BPR) * 4;
+      uint32_t m4 = 0;
+      if (ly < h && lx0 < w) m4 = mask[((int64_t)(y0 + ly) * W + x0 + lx0) >> 2];
+      uint32_t out = 0;
 #pragma unroll
-    for (int seg = 0; seg < SEGS; ++seg) {
-      const int sidx = ly * TILE_W + seg * 32 + lane;
-      const uint32_t east = __ballot_sync(FULL, bits[sidx] & 1u);
-      const uint32_t breaks = ~east & ((1u << lane) - 1u);   // lanes below me not joined to their right
-      const int start = breaks ? 32 - __clz(breaks) : 0;
-      const int root = (start == 0 && carry >= 0) ? carry : ly * TILE_W + seg * 32 + start;
-      par[sidx] = root;
-      const int root31 = __shfl_sync(FULL, root, 31);
-      carry = (east >> 31) ? root31 : -1;
-    }
-  }
-  __syncthreads();
-
-  // 3. north bonds inside the tile
-  for (int ly = warp; ly < TILE_H - 1; ly += NWARPS) {
-#pragma unroll
-    for (int seg = 0; seg < SEGS; ++seg) {
-      const int lx = seg * 32 + lane;
-      const int sidx = ly * TILE_W + lx;
-      const uint32_t b = bits[sidx];
-      if (b & 2u) {
-        bool redundant = false;
-        if (lx > 0) {
-          const uint32_t bl = bits[sidx - 1], bu = bits[sidx - 1 + TILE_W];
-          redundant = (bl & 2u) && (bl & 1u) && (bu & 1u);
-        }
-        if (!redundant) sm_union(par, sidx, sidx + TILE_W, TILE_SITES, s.err);
+      for (int j = 0; j < 4; ++j) {
+        const int lx = lx0 + j;
+        if (ly < h && lx < w) out |= tile_bits((m4 >> (2 * j)) & 3u, lx, ly, w, h) << (8 * j);
       }
+      *reinterpret_cast<uint32_t*>(bits + ly * TILE_W + lx0) = out;
     }
+  } else {
+    for (int sidx = threadIdx.x; sidx < TILE_SITES; sidx += LABEL_THREADS) {
+      const int ly = sidx >> TILE_W_LOG2, lx = sidx & (TILE_W - 1);
+      uint32_t b = 0;
+      if (ly < h && lx < w) b = tile_bits(site_bits(mask, (int64_t)(y0 + ly) * W + x0 + lx), lx, ly, w, h);
+      bits[sidx] = (uint8_t)b;
+    }
+  }
+  __syncthreads();
+
+  // 2. strip sweep
+  {
+    const int col = warp * 32 + lane;
+    const unsigned below_lanes = (1u << lane) - 1u;
+    int lab_below = 0;
+    bool up_open = false;       // north bond from the site below into this lane's site
+    for (int ly = 0; ly < h; ++ly) {
+      const int sidx = ly * TILE_W + col;
+      const uint32_t b = bits[sidx];
+      const uint32_t east = __ballot_sync(FULL, b & 1u) & 0x7FFFFFFFu;   // runs stay inside the strip
+      const uint32_t breaks = ~east & below_lanes;
+      const int start = breaks ? 32 - __clz(breaks) : 0;
+      const int end = lane + __ffs(~east >> lane) - 1;
+      const int up = up_open ? lab_below : INT_MAX;
+      int m = up;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int v = __shfl_up_sync(FULL, m, d);
+        if (lane - d >= start) m = min(m, v);
+      }
+      const int mrun = __shfl_sync(FULL, m, end);
+      const int label = (mrun == INT_MAX) ? ly * TILE_W + warp * 32 + start : mrun;
+      par[sidx] = label;
+      __syncwarp();
+      const int up_left = __shfl_up_sync(FULL, up, 1);
+      if (up != INT_MAX && up != label && !(lane > start && up_left == up))
+        sm_union(par, up, label, TILE_SITES, s.err);
+      __syncwarp();
+      lab_below = label;
+      up_open = (b & 2u) != 0;
+    }
+  }
+  __syncthreads();
+
+  // 3. east bonds between strips
+  constexpr int STRIPS = TILE_W / 32;
+  for (int k = threadIdx.x; k < TILE_H * (STRIPS - 1); k += LABEL_THREADS) {
+    const int ly = k / (STRIPS - 1), c = k - ly * (STRIPS - 1);
+    if (ly >= h) continue;
+    const int a = ly * TILE_W + c * 32 + 31;
+    if (!(bits[a] & 1u)) continue;
+    if (ly > 0) {
+      const int a0 = a - TILE_W;
+      if ((bits[a0] & 1u) && (bits[a0] & 2u) && (bits[a0 + 1] & 2u)) continue;   // joined below
+    }
+    sm_union(par, a, a + 1, TILE_SITES, s.err);
   }
   __syncthreads();
 

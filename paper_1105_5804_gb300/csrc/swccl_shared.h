@@ -12,12 +12,12 @@ namespace swccl {
 enum : uint32_t { TAG_BOND = 0, TAG_FLIP = 1, TAG_INIT = 2, TAG_PERC = 3 };
 
 // Tile of the local labeling phase: TILE_H rows x TILE_W columns, one CTA
-// of LABEL_THREADS threads per tile.  TILE_W and TILE_H are multiples of 32;
-// TILE_W is a power of two.
-constexpr int TILE_H = 64;
-constexpr int TILE_W = 128;
-constexpr int TILE_W_LOG2 = 7;
-constexpr int LABEL_THREADS = 512;
+// per tile with one warp per 32-column strip (LABEL_THREADS = TILE_W).
+// TILE_W is a power of two and a multiple of 32; TILE_H a multiple of 32.
+constexpr int TILE_H = 32;
+constexpr int TILE_W = 256;
+constexpr int TILE_W_LOG2 = 8;
+constexpr int LABEL_THREADS = TILE_W;
 
 // Per-tile seam record written by the local labeling phase and read by the
 // merge: labels of the four tile edges and the raw bond bits leaving the
