@@ -196,6 +196,31 @@ int ccl_bonds_from_pixels(const uint8_t* px, uint8_t* mask, int H, int W, int pe
  * ceil(H*W/4) bytes. */
 int ccl_perc_mask(uint64_t k, uint8_t* mask, int H, int W, void* stream);
 
+/* Bytes of the fixed scratch array of ccl_label_noalloc (64 MiB).  Every GPU
+ * that loads the library holds this much device memory until the process
+ * exits.  A grid fits when ccl_workspace_bytes(H, W) is not larger, about
+ * 4.3 bytes per site: up to about 14.7 million sites, e.g. 3840 x 3840. */
+#define CCL_NOALLOC_SCRATCH_BYTES (64LL << 20)
+
+/* ccl_label for callers that cannot allocate device memory when they label:
+ * code running while a stream is captured into a CUDA graph in global
+ * capture mode (cudaMalloc is refused there), latency-bound loops that must
+ * not call cudaMalloc/cudaFree (cudaFree synchronises the whole device), and
+ * programs whose device memory belongs to another framework's allocator.
+ * The paper has no counterpart: it is a deployment variant of ccl_label.
+ * Same arguments, layout and result as ccl_label; no cudaMalloc, cudaFree or
+ * other allocating call is made.  Its scratch is one file-scope device array
+ * of CCL_NOALLOC_SCRATCH_BYTES shared by all calls on a device, which keeps
+ * the last call's contents (the kernels overwrite every part they read, so
+ * nothing needs clearing).  Consequently two calls whose work overlaps on
+ * the GPU (different streams, not ordered) race on that array and give
+ * wrong labels: order them.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current);
+ * make that first call before any stream capture.  Grids whose scratch
+ * exceeds CCL_NOALLOC_SCRATCH_BYTES are rejected with SW_ERR_ARG before
+ * anything is launched.  Device-side failures are reported by ccl_status(). */
+int ccl_label_noalloc(const uint8_t* bond_mask, int32_t* labels, int H, int W, int periodic, void* stream);
+
 /* Wait for the whole device and return the first device-side failure
  * recorded by ccl_* kernels since the last call (SW_OK if none); clears it. */
 int ccl_status(void);

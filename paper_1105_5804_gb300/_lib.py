@@ -60,6 +60,7 @@ def lib():
         "ccl_label_ws": ([vp, vp, i32, i32, i32, vp, i64, vp], i32),
         "ccl_bonds_from_pixels": ([vp, vp, i32, i32, i32, vp], i32),
         "ccl_perc_mask": ([u64, vp, i32, i32, vp], i32),
+        "ccl_label_noalloc": ([vp, vp, i32, i32, i32, vp], i32),
         "ccl_status": ([], i32),
     }
     for name, (args, res) in sig.items():
@@ -257,6 +258,20 @@ def ccl_perc_mask(k, mask, H, W, stream=None):
     _check(lib().ccl_perc_mask(k, _dev(mask, torch.uint8, mask_bytes(H * W), "mask"), H, W,
                                _stream(stream)))
     return mask
+
+
+CCL_NOALLOC_SCRATCH_BYTES = 64 << 20
+
+
+def ccl_label_noalloc(bond_mask, labels, H, W, periodic, stream=None):
+    """ccl_label without any allocation (fixed device scratch array); see
+    include/swccl.h for who needs it and its size limit."""
+    import torch
+    N = H * W
+    _check(lib().ccl_label_noalloc(_dev(bond_mask, torch.uint8, mask_bytes(N), "bond_mask"),
+                                   _dev(labels, torch.int32, N, "labels"), H, W, 1 if periodic else 0,
+                                   _stream(stream)))
+    return labels
 
 
 def ccl_status():

@@ -45,6 +45,22 @@ constexpr int OBS_CAP = 4096;
 // Device status word of the stand-alone labeling calls.
 __device__ int g_ccl_status;
 
+namespace {
+int* ccl_status_ptr() {
+  static int* ptrs[64] = {nullptr};
+  static std::mutex mu;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!ptrs[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_ccl_status) != cudaSuccess) return nullptr;
+    ptrs[dev] = static_cast<int*>(p);
+  }
+  return ptrs[dev];
+}
+}  // namespace
+
 struct sw_handle {
   int L = 0, q = 0;
   uint64_t T = 0, seed = 0;
@@ -132,6 +148,11 @@ uint64_t threshold_of(double K) {
 }
 
 }  // namespace
+
+namespace swccl {
+int set_last_error(int code, const std::string& msg) { return fail(code, msg); }
+int* ccl_status_word() { return ccl_status_ptr(); }
+}  // namespace swccl
 
 extern "C" {
 
@@ -378,19 +399,6 @@ int ccl_validate(const void* mask, const void* labels, int H, int W) {
   return SW_OK;
 }
 
-int* ccl_status_ptr() {
-  static int* ptrs[64] = {nullptr};
-  static std::mutex mu;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-  std::lock_guard<std::mutex> lock(mu);
-  if (!ptrs[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_ccl_status) != cudaSuccess) return nullptr;
-    ptrs[dev] = static_cast<int*>(p);
-  }
-  return ptrs[dev];
-}
 }  // namespace
 
 int64_t ccl_workspace_bytes(int H, int W) {

@@ -2,6 +2,8 @@
 // translation units of libswccl (not part of the public ABI).
 #pragma once
 #include <cstdint>
+#include <string>
+
 #include <cuda_runtime.h>
 
 #include "../../include/swccl.h"
@@ -95,5 +97,11 @@ cudaError_t launch_site_compress(int32_t* labels, int64_t n_sites, cudaStream_t 
 cudaError_t launch_flip(int8_t* spins, const int32_t* labels, int L, int q, const SwCtl* ctl,
                         int64_t* obs_ring, int obs_cap, cudaStream_t st);
 cudaError_t launch_advance(SwCtl* ctl, cudaStream_t st);
+
+// Host helpers of the C ABI: set this thread's sw_last_error() message and
+// return `code`; device address of the stand-alone labeling status word on
+// the current device (nullptr on failure).
+int set_last_error(int code, const std::string& msg);
+int* ccl_status_word();
 
 }  // namespace swccl
