@@ -172,7 +172,7 @@ int sw_phase_times(sw_handle* h, double* ms, int64_t* n_sweeps);
  * periodic == 0: those bonds are ignored (image segmentation).
  * Requires H, W >= 1 and H*W < 2^31.  Enqueued on `stream` (a
  * cudaStream_t, NULL = legacy default stream); returns without waiting.
- * Scratch memory (about 4.1 bytes per site) is taken with cudaMallocAsync
+ * Scratch memory (about 8.3 bytes per site) is taken with cudaMallocAsync
  * on the same stream and released in stream order. */
 int ccl_label(const uint8_t* bond_mask, int32_t* labels, int H, int W, int periodic, void* stream);
 
@@ -199,7 +199,7 @@ int ccl_perc_mask(uint64_t k, uint8_t* mask, int H, int W, void* stream);
 /* Bytes of the fixed scratch array of ccl_label_noalloc (64 MiB).  Every GPU
  * that loads the library holds this much device memory until the process
  * exits.  A grid fits when ccl_workspace_bytes(H, W) is not larger, about
- * 4.3 bytes per site: up to about 14.7 million sites, e.g. 3840 x 3840. */
+ * 8.3 bytes per site: up to about 7.9 million sites, e.g. 2816 x 2816. */
 #define CCL_NOALLOC_SCRATCH_BYTES (64LL << 20)
 
 /* ccl_label for callers that cannot allocate device memory when they label:

@@ -39,38 +39,41 @@ constexpr int TILE_SITES = TILE_H * TILE_W;
 constexpr unsigned FULL = 0xFFFFFFFFu;
 }  // namespace
 
-// Shared-memory bond bits per tile site: bit 0 east bond inside the tile,
-// bit 1 north bond inside the tile, bits 2..3 the raw mask bits.
-__device__ __forceinline__ uint32_t tile_bits(uint32_t m, int lx, int ly, int w, int h) {
-  uint32_t b = m << 2;
-  if ((m & 1u) && lx + 1 < w) b |= 1u;
-  if ((m & 2u) && ly + 1 < h) b |= 2u;
-  return b;
-}
-
-// Local labeling of one tile.
-//  1. the tile's bond bits go to shared memory;
-//  2. warp c sweeps its 32-column strip from row 0 upwards.  The labels of
-//     the row below stay in registers.  A row is cut into runs of
-//     east-joined sites with one ballot; each run takes the smallest label
-//     among the sites below it that reach it by a north bond (a segmented
-//     minimum over the run's lanes, five shuffle steps), or, if none does, a
-//     fresh label: the index of its first site.  Only a run reached from
-//     below by two different labels joins them, with the shared-memory
-//     union-find; every other site is labeled without an atomic.
-//  3. east bonds between strips are joined with the union-find, skipping a
-//     bond whose two ends were already joined through the row below;
-//  4. every site resolves its root; the root is the smallest index of the
-//     tile component (a fresh label is always a run's first site, the
-//     component's smallest site starts a run nothing reaches from below, and
-//     unions hook the larger root under the smaller), so its global index is
-//     the minimum site index of the tile component.
+// Local labeling of one tile (TILE_H x TILE_W sites, one warp per 32-column
+// strip).
+//  1. the tile's bond bits are copied to shared memory as they are packed in
+//     the mask, one 64-bit word (32 sites x {east, north}) per row and strip;
+//     bits of sites outside the grid and the east bond of the tile's last
+//     column are cleared;
+//  2. warp c sweeps its strip from row 0 upwards with the labels of the row
+//     below in registers.  A row is cut into runs of east-joined sites with
+//     one ballot.  A run reached from below through north bonds takes the
+//     label of its leftmost such site (one shuffle); a run nothing reaches
+//     gets a fresh label, the index of its first site (a union-find node).
+//     A lane reached from below by a label other than its run's appends the
+//     pair to its warp's list: no union-find work happens inside the sweep;
+//  3. the east bonds between strips and all listed pairs are joined by all
+//     threads at once with the shared-memory union-find (hooks larger roots
+//     under smaller ones); hooked roots are logged;
+//  4. logged roots resolve their final roots; every site's label is a node,
+//     so its root is par[par[site]].  The root is the smallest index of the
+//     tile component: the component's smallest site starts a run nothing
+//     reaches from below, so it is a node, and a smaller root never hooks
+//     under a larger one.  Its global index is therefore the minimum site
+//     index of the tile component.  Roots are listed per tile.
+//  5. the labels and outgoing bond bits of the four tile edges go to the
+//     tile's seam record.
 __global__ void __launch_bounds__(LABEL_THREADS)
 k_tile_label(const uint8_t* __restrict__ mask, int32_t* __restrict__ labels, Grid g,
              LabelScratch s) {
+  constexpr int STRIPS = TILE_W / 32;
+  constexpr int PAIR_CAP = TILE_SITES / STRIPS;   // per warp: (TILE_H - 1) * 32 pairs at most
+  static_assert((TILE_H - 1) * 32 <= PAIR_CAP, "pair list capacity");
   __shared__ int par[TILE_SITES];
-  __shared__ __align__(16) uint8_t bits[TILE_SITES];
-  __shared__ int n_roots;
+  __shared__ unsigned long long mb[TILE_H * STRIPS];
+  __shared__ int warp_count[STRIPS];
+  __shared__ int warp_roots[LABEL_THREADS / 32];
+  __shared__ int n_hooked;
 
   const int t = blockIdx.x;
   const int ty = t / g.tiles_x, tx = t - ty * g.tiles_x;
@@ -78,31 +81,26 @@ k_tile_label(const uint8_t* __restrict__ mask, int32_t* __restrict__ labels, Gri
   const int h = min(TILE_H, g.H - y0), w = min(TILE_W, g.W - x0);
   const int W = g.W;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) n_roots = 0;
+  int32_t* slot = s.roots + (int64_t)t * TILE_SITES;     // pair lists, later the root list
+  int32_t* hook_log = s.work + (int64_t)t * TILE_SITES;
+  if (threadIdx.x == 0) n_hooked = 0;
 
-  // 1. bond bits of the tile
-  if ((W & 3) == 0) {
-    // rows start on mask-byte boundaries: one byte = four sites per thread
-    constexpr int BPR = TILE_W / 4;
-    for (int k = threadIdx.x; k < BPR * TILE_H; k += LABEL_THREADS) {
-      const int ly = k / BPR, lx0 = (k - ly * BPR) * 4;
-      uint32_t m4 = 0;
-      if (ly < h && lx0 < w) m4 = mask[((int64_t)(y0 + ly) * W + x0 + lx0) >> 2];
-      uint32_t out = 0;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int lx = lx0 + j;
-        if (ly < h && lx < w) out |= tile_bits((m4 >> (2 * j)) & 3u, lx, ly, w, h) << (8 * j);
+  // 1. bond bits
+  for (int k = threadIdx.x; k < TILE_H * STRIPS; k += LABEL_THREADS) {
+    const int ly = k / STRIPS, c = k - ly * STRIPS;
+    const int nvalid = min(max(w - 32 * c, 0), 32);
+    unsigned long long wd = 0ull;
+    if (ly < h && nvalid > 0) {
+      const int64_t site0 = (int64_t)(y0 + ly) * W + x0 + 32 * c;
+      if ((W & 31) == 0 && (reinterpret_cast<uintptr_t>(mask) & 7) == 0) {
+        wd = reinterpret_cast<const unsigned long long*>(mask)[site0 >> 5];
+      } else {
+        for (int i = 0; i < nvalid; ++i) wd |= (unsigned long long)site_bits(mask, site0 + i) << (2 * i);
       }
-      *reinterpret_cast<uint32_t*>(bits + ly * TILE_W + lx0) = out;
+      if (nvalid < 32) wd &= (1ull << (2 * nvalid)) - 1ull;
+      if (32 * c + nvalid == w) wd &= ~(1ull << (2 * (nvalid - 1)));   // east bond leaving the tile
     }
-  } else {
-    for (int sidx = threadIdx.x; sidx < TILE_SITES; sidx += LABEL_THREADS) {
-      const int ly = sidx >> TILE_W_LOG2, lx = sidx & (TILE_W - 1);
-      uint32_t b = 0;
-      if (ly < h && lx < w) b = tile_bits(site_bits(mask, (int64_t)(y0 + ly) * W + x0 + lx), lx, ly, w, h);
-      bits[sidx] = (uint8_t)b;
-    }
+    mb[k] = wd;
   }
   __syncthreads();
 
@@ -110,93 +108,138 @@ k_tile_label(const uint8_t* __restrict__ mask, int32_t* __restrict__ labels, Gri
   {
     const int col = warp * 32 + lane;
     const unsigned below_lanes = (1u << lane) - 1u;
+    int32_t* pairs = slot + warp * PAIR_CAP;
+    int n_pairs = 0;
     int lab_below = 0;
     bool up_open = false;       // north bond from the site below into this lane's site
     for (int ly = 0; ly < h; ++ly) {
-      const int sidx = ly * TILE_W + col;
-      const uint32_t b = bits[sidx];
+      const uint32_t b = (uint32_t)(mb[ly * STRIPS + warp] >> (2 * lane)) & 3u;
       const uint32_t east = __ballot_sync(FULL, b & 1u) & 0x7FFFFFFFu;   // runs stay inside the strip
+      const uint32_t upb = __ballot_sync(FULL, up_open);
       const uint32_t breaks = ~east & below_lanes;
       const int start = breaks ? 32 - __clz(breaks) : 0;
       const int end = lane + __ffs(~east >> lane) - 1;
-      const int up = up_open ? lab_below : INT_MAX;
-      int m = up;
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const int v = __shfl_up_sync(FULL, m, d);
-        if (lane - d >= start) m = min(m, v);
-      }
-      const int mrun = __shfl_sync(FULL, m, end);
-      const int label = (mrun == INT_MAX) ? ly * TILE_W + warp * 32 + start : mrun;
-      par[sidx] = label;
-      __syncwarp();
-      const int up_left = __shfl_up_sync(FULL, up, 1);
-      if (up != INT_MAX && up != label && !(lane > start && up_left == up))
-        sm_union(par, up, label, TILE_SITES, s.err);
-      __syncwarp();
+      const uint32_t run = ((2u << end) - 1u) & ~((1u << start) - 1u);
+      const uint32_t reach = upb & run;
+      const int first = reach ? __ffs(reach) - 1 : lane;
+      const int from_below = __shfl_sync(FULL, lab_below, first);
+      const int label = reach ? from_below : ly * TILE_W + warp * 32 + start;
+      par[ly * TILE_W + col] = label;
+      const int lab_left = __shfl_up_sync(FULL, lab_below, 1);
+      const bool dup = lane > start && ((upb >> (lane - 1)) & 1u) && lab_left == lab_below;
+      const bool pair = up_open && lab_below != label && !dup;
+      const uint32_t pm = __ballot_sync(FULL, pair);
+      if (pair) pairs[n_pairs + __popc(pm & below_lanes)] = (lab_below << 16) | label;
+      n_pairs += __popc(pm);
       lab_below = label;
       up_open = (b & 2u) != 0;
     }
+    if (lane == 0) warp_count[warp] = n_pairs;
   }
   __syncthreads();
 
-  // 3. east bonds between strips
-  constexpr int STRIPS = TILE_W / 32;
-  for (int k = threadIdx.x; k < TILE_H * (STRIPS - 1); k += LABEL_THREADS) {
-    const int ly = k / (STRIPS - 1), c = k - ly * (STRIPS - 1);
-    if (ly >= h) continue;
-    const int a = ly * TILE_W + c * 32 + 31;
-    if (!(bits[a] & 1u)) continue;
-    if (ly > 0) {
-      const int a0 = a - TILE_W;
-      if ((bits[a0] & 1u) && (bits[a0] & 2u) && (bits[a0 + 1] & 2u)) continue;   // joined below
+  // 3. joins: east bonds between strips, then the listed pairs
+  {
+    int total = 0;
+#pragma unroll
+    for (int k = 0; k < STRIPS; ++k) total += warp_count[k];
+    constexpr int SEAMS = TILE_H * (STRIPS - 1);
+    for (int k = threadIdx.x; k < SEAMS + total; k += LABEL_THREADS) {
+      int a, b;
+      if (k < SEAMS) {
+        const int ly = k / (STRIPS - 1), c = k - ly * (STRIPS - 1);
+        if (ly >= h) continue;
+        if (!((mb[ly * STRIPS + c] >> 62) & 1ull)) continue;
+        if (ly > 0) {
+          const unsigned long long lo = mb[(ly - 1) * STRIPS + c], hi = mb[(ly - 1) * STRIPS + c + 1];
+          if (((lo >> 62) & 1ull) && ((lo >> 63) & 1ull) && ((hi >> 1) & 1ull)) continue;   // joined below
+        }
+        a = ly * TILE_W + c * 32 + 31;
+        b = a + 1;
+      } else {
+        int j = k - SEAMS, wsel = 0;
+        while (j >= warp_count[wsel]) j -= warp_count[wsel++];
+        const int v = slot[wsel * PAIR_CAP + j];
+        a = v >> 16;
+        b = v & 0xFFFF;
+      }
+      sm_union_log(par, a, b, TILE_SITES, s.err, hook_log, &n_hooked, TILE_SITES);
     }
-    sm_union(par, a, a + 1, TILE_SITES, s.err);
   }
   __syncthreads();
 
-  // 4. final tile roots -> global labels; collect roots
-  const int64_t tile_base = (int64_t)t * TILE_SITES;
-  for (int sidx = threadIdx.x; sidx < TILE_SITES; sidx += LABEL_THREADS) {
+  // 4a. hooked roots resolve their final roots (every other node is a root)
+  {
+    const int nh = min(n_hooked, TILE_SITES);
+    for (int k = threadIdx.x; k < nh; k += LABEL_THREADS) {
+      const int x = hook_log[k];
+      const int r = sm_find(par, x, TILE_SITES, s.err);
+      atomicMin(&par[x], r);
+    }
+  }
+  __syncthreads();
+
+  // 4b. every site's root; global labels; root list
+  constexpr int PER_T = TILE_SITES / LABEL_THREADS;
+  uint32_t mine = 0;      // bit j: site threadIdx.x + j*LABEL_THREADS is a root
+#pragma unroll 4
+  for (int j = 0; j < PER_T; ++j) {
+    const int sidx = threadIdx.x + j * LABEL_THREADS;
     const int ly = sidx >> TILE_W_LOG2, lx = sidx & (TILE_W - 1);
-    const bool inside = ly < h && lx < w;
-    int r = sidx, gr = 0;
-    if (inside) {
-      r = sm_find(par, sidx, TILE_SITES, s.err);
-      atomicMin(&par[sidx], r);
-      gr = (y0 + (r >> TILE_W_LOG2)) * W + x0 + (r & (TILE_W - 1));
-      labels[(int64_t)(y0 + ly) * W + x0 + lx] = gr;
+    if (ly < h && lx < w) {
+      const int p = par[sidx];
+      const int r = par[p];
+      labels[(int64_t)(y0 + ly) * W + x0 + lx] = (y0 + (r >> TILE_W_LOG2)) * W + x0 + (r & (TILE_W - 1));
+      if (r == sidx) mine |= 1u << j;
     }
-    const bool is_root = inside && r == sidx;
-    const uint32_t rb = __ballot_sync(FULL, is_root);
-    int base = 0;
-    if (lane == 0 && rb) base = atomicAdd(&n_roots, __popc(rb));
-    base = __shfl_sync(FULL, base, 0);
-    if (is_root) s.roots[tile_base + base + __popc(rb & ((1u << lane) - 1u))] = gr;
   }
+  int cnt = __popc(mine), incl = cnt;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int v = __shfl_up_sync(FULL, incl, d);
+    if (lane >= d) incl += v;
+  }
+  if (lane == 31) warp_roots[warp] = incl;
   __syncthreads();
+  int base = 0, total = 0;
+#pragma unroll
+  for (int k = 0; k < LABEL_THREADS / 32; ++k) {
+    const int c = warp_roots[k];
+    base += (k < warp) ? c : 0;
+    total += c;
+  }
+  base += incl - cnt;
+  while (mine) {
+    const int j = __ffs(mine) - 1;
+    mine &= mine - 1;
+    const int sidx = threadIdx.x + j * LABEL_THREADS;
+    slot[base++] =
+        (y0 + (sidx >> TILE_W_LOG2)) * W + x0 + (sidx & (TILE_W - 1));
+  }
 
   // 5. seam record
   int32_t* rec = s.seams + (int64_t)t * SeamLayout::INTS;
   auto glabel = [&](int ly, int lx) -> int32_t {
-    const int r = par[ly * TILE_W + lx];
+    const int r = par[par[ly * TILE_W + lx]];
     return (y0 + (r >> TILE_W_LOG2)) * W + x0 + (r & (TILE_W - 1));
   };
   for (int k = threadIdx.x; k < TILE_H; k += LABEL_THREADS) {
     const bool ok = k < h;
     rec[SeamLayout::COL_L + k] = ok ? glabel(k, 0) : -1;
     rec[SeamLayout::COL_R + k] = ok ? glabel(k, w - 1) : -1;
-    const uint32_t eb = __ballot_sync(FULL, ok && (bits[k * TILE_W + w - 1] & 4u));
+    const bool e = ok && (site_bits(mask, (int64_t)(y0 + k) * W + x0 + w - 1) & 1u);
+    const uint32_t eb = __ballot_sync(FULL, e);
     if (lane == 0) rec[SeamLayout::E_BITS + (k >> 5)] = (int32_t)eb;
   }
   for (int k = threadIdx.x; k < TILE_W; k += LABEL_THREADS) {
     const bool ok = k < w;
     rec[SeamLayout::ROW_B + k] = ok ? glabel(0, k) : -1;
     rec[SeamLayout::ROW_T + k] = ok ? glabel(h - 1, k) : -1;
-    const uint32_t nb = __ballot_sync(FULL, ok && (bits[(h - 1) * TILE_W + k] & 8u));
+    const bool n = ok && ((mb[(h - 1) * STRIPS + (k >> 5)] >> (2 * (k & 31) + 1)) & 1ull);
+    const uint32_t nb = __ballot_sync(FULL, n);
     if (lane == 0) rec[SeamLayout::N_BITS + (k >> 5)] = (int32_t)nb;
   }
-  if (threadIdx.x == 0) s.root_counts[t] = n_roots;
+  if (threadIdx.x == 0) s.root_counts[t] = total;
 }
 
 cudaError_t launch_tile_label(const uint8_t* mask, int32_t* labels, const Grid& g,
@@ -311,7 +354,7 @@ cudaError_t launch_site_compress(int32_t* labels, int64_t n_sites, cudaStream_t 
 int64_t label_scratch_bytes(const Grid& g) {
   auto al = [](int64_t b) { return (b + 255) & ~(int64_t)255; };
   const int64_t nt = g.n_tiles();
-  return al(nt * TILE_SITES * 4) + al(nt * 4) + al(nt * SeamLayout::INTS * 4) + al(4);
+  return 2 * al(nt * TILE_SITES * 4) + al(nt * 4) + al(nt * SeamLayout::INTS * 4) + al(4);
 }
 
 LabelScratch carve_label_scratch(const Grid& g, void* base, int* err) {
@@ -320,6 +363,8 @@ LabelScratch carve_label_scratch(const Grid& g, void* base, int* err) {
   char* p = static_cast<char*>(base);
   LabelScratch s;
   s.roots = reinterpret_cast<int32_t*>(p);
+  p += al(nt * TILE_SITES * 4);
+  s.work = reinterpret_cast<int32_t*>(p);
   p += al(nt * TILE_SITES * 4);
   s.root_counts = reinterpret_cast<int32_t*>(p);
   p += al(nt * 4);

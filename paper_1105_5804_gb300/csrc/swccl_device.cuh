@@ -96,6 +96,28 @@ __device__ __forceinline__ void sm_union(int* par, int a, int b, int limit, int*
   set_error(err, SW_ERR_STATE);
 }
 
+// As sm_union; a root that gets hooked is appended to `hooked` (count in
+// *n_hooked, capacity `cap`), so that only hooked nodes need resolving later.
+__device__ __forceinline__ void sm_union_log(int* par, int a, int b, int limit, int* err, int* hooked,
+                                             int* n_hooked, int cap) {
+  volatile int* vp = par;
+  for (int rounds = 0; rounds <= limit; ++rounds) {
+    a = sm_find(vp, a, limit, err);
+    b = sm_find(vp, b, limit, err);
+    if (a == b) return;
+    if (a > b) { const int t = a; a = b; b = t; }
+    const int old = atomicMin(&par[b], a);
+    if (old == b) {
+      const int k = atomicAdd(n_hooked, 1);
+      if (k < cap) hooked[k] = b;
+      else set_error(err, SW_ERR_STATE);
+      return;
+    }
+    b = old;
+  }
+  set_error(err, SW_ERR_STATE);
+}
+
 // ---------------------------------------------------------------------------
 // Union-find on a global int32 array (the label array itself: the entry of a
 // tile root is its parent pointer).  Loads bypass L1 (ld.cg) because other

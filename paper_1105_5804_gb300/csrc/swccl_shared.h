@@ -55,7 +55,8 @@ inline Grid make_grid(int H, int W, int periodic) {
 
 // Scratch of one labeling problem.
 struct LabelScratch {
-  int32_t* roots;        // n_tiles * TILE_H * TILE_W: tile-root lists
+  int32_t* roots;        // n_tiles * TILE_H * TILE_W: pair lists, then tile-root lists
+  int32_t* work;         // n_tiles * TILE_H * TILE_W: per-tile log of hooked roots
   int32_t* root_counts;  // n_tiles
   int32_t* seams;        // n_tiles * SeamLayout::INTS
   int* err;              // device status word

@@ -84,6 +84,6 @@ def test_workspace_size_validation():
     assert sw.ccl_workspace_bytes(0, 5) == -1
     assert sw.ccl_workspace_bytes(1 << 16, 1 << 16) == -1
     assert sw.ccl_workspace_bytes(1, 1) > 0
-    # about 4 bytes per site of root lists plus small seam records
+    # two int32 per site (pair lists / root lists, hook logs) plus small seam records
     b = sw.ccl_workspace_bytes(4096, 4096)
-    assert 4 * 4096 * 4096 <= b < 4.5 * 4096 * 4096
+    assert 8 * 4096 * 4096 <= b < 8.5 * 4096 * 4096
