@@ -72,6 +72,20 @@ extern "C" {
 #define SW_PHASE_FLIP 4      /* cluster flip + observables      (Sec. II.D)   */
 #define SW_N_PHASES 5
 
+/* How a handle runs a sweep (sw_set_mode).  Both compute the same chain,
+ * bit for bit.
+ *   SW_MODE_FUSED (default): the bonds are drawn inside the labeling kernel
+ *     (the draws are counter-based, so they can be made where they are
+ *     used); neither the bond mask nor per-site int32 labels go through
+ *     device memory: three kernels per sweep.  Phase times: the drawing and
+ *     local labeling kernel counts as SW_PHASE_LOCAL, the flip kernel (root
+ *     lookup, draws, spins) as SW_PHASE_FLIP; ACTIVATE and ROOTS are zero.
+ *   SW_MODE_STAGED: one kernel per step (activation writing the packed
+ *     mask, local labeling writing int32 labels, merge, root compression,
+ *     flip); required by sw_debug_dump. */
+#define SW_MODE_STAGED 0
+#define SW_MODE_FUSED 1
+
 typedef struct sw_handle sw_handle;
 
 /* Message of the last failed call on this host thread ("" if none).  The
@@ -91,8 +105,9 @@ uint64_t sw_threshold_for(int q, double beta, double J, int convention);
  * J = 1, SW_CONV_AUTO, cold start (every s = 0), its own CUDA stream.
  * Requirements: 4 <= L <= 46340, L % 4 == 0; 2 <= q <= 127; beta >= 0.
  * The library owns all device memory of the chain (spins, mask, labels,
- * root lists, seam records, a ring of per-sweep observables); about
- * 10.5 bytes per site.  Returns NULL on failure (see sw_last_error()). */
+ * 16-bit tile roots, root lists, seam records, a ring of per-sweep
+ * observables); about 15.8 bytes per site.  Sweeps run in SW_MODE_FUSED.
+ * Returns NULL on failure (see sw_last_error()). */
 sw_handle* sw_create(int L, int q, double beta, uint64_t seed);
 
 /* As sw_create with explicit coupling J, convention (SW_CONV_*), hot start
@@ -141,13 +156,18 @@ int sw_set_spins(sw_handle* h, const int8_t* src, int is_device);
 
 /* Copy the bond mask (ceil(L*L/4) bytes, packed as above) and the canonical
  * labels (int32[L*L]) of the last completed sweep, for bit-exact checks.
- * Either pointer may be NULL.  SW_ERR_STATE if no sweep ran since creation
- * or since the last host sw_set_spins.  Synchronises. */
+ * Either pointer may be NULL.  SW_ERR_STATE if the last sweep did not run in
+ * SW_MODE_STAGED, or no sweep ran since creation or since the last host
+ * sw_set_spins.  Synchronises. */
 int sw_debug_dump(sw_handle* h, uint8_t* mask_out, int32_t* labels_out, int is_device);
 
 /* info[0..7] = L, q, T, seed, sweeps enqueued so far, observable ring
  * capacity, tile height, tile width. */
 int sw_get_info(sw_handle* h, int64_t* info);
+
+/* Select SW_MODE_STAGED or SW_MODE_FUSED for the following sweeps (see
+ * above); the chain continues unchanged.  Synchronises. */
+int sw_set_mode(sw_handle* h, int mode);
 
 /* The CUDA stream (cudaStream_t) all work of the handle is ordered on. */
 void* sw_stream(sw_handle* h);

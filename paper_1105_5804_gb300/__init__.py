@@ -8,11 +8,11 @@ library; the first call does, and raises if it was not built.
 """
 from ._lib import (  # noqa: F401
     SW_OK, SW_ERR_ARG, SW_ERR_OOM, SW_ERR_CUDA, SW_ERR_TIMEOUT, SW_ERR_STATE,
-    SW_CONV_AUTO, SW_CONV_POTTS, SW_CONV_ISING, SW_N_PHASES, PHASE_NAMES,
+    SW_CONV_AUTO, SW_CONV_POTTS, SW_CONV_ISING, SW_N_PHASES, PHASE_NAMES, SW_MODE_STAGED, SW_MODE_FUSED,
     SwcclError, lib, mask_bytes,
     sw_last_error, sw_threshold_for, sw_create, sw_create_ex, sw_create_threshold, sw_destroy,
     sw_sweep, sw_sync, sw_observables, sw_get_spins, sw_set_spins, sw_debug_dump, sw_get_info,
-    sw_stream, sw_set_timing, sw_phase_times,
+    sw_stream, sw_set_timing, sw_phase_times, sw_set_mode,
     ccl_label, ccl_workspace_bytes, ccl_label_ws, ccl_bonds_from_pixels, ccl_perc_mask, ccl_status,
     ccl_label_noalloc, CCL_NOALLOC_SCRATCH_BYTES,
 )
@@ -31,6 +31,9 @@ class SwendsenWang:
 
     def sweep(self, n=1):
         sw_sweep(self.h, n)
+
+    def set_mode(self, mode):
+        sw_set_mode(self.h, mode)
 
     def observables(self, max_sweeps=4096):
         return sw_observables(self.h, max_sweeps)

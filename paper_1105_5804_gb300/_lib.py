@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libswccl.so")
 SW_OK, SW_ERR_ARG, SW_ERR_OOM, SW_ERR_CUDA, SW_ERR_TIMEOUT, SW_ERR_STATE = 0, 1, 2, 3, 4, 5
 SW_CONV_AUTO, SW_CONV_POTTS, SW_CONV_ISING = 0, 1, 2
 SW_N_PHASES = 5
+SW_MODE_STAGED, SW_MODE_FUSED = 0, 1
 PHASE_NAMES = ("activate", "local", "merge", "roots", "flip")
 
 
@@ -54,6 +55,7 @@ def lib():
         "sw_get_info": ([vp, vp], i32),
         "sw_stream": ([vp], vp),
         "sw_set_timing": ([vp, i32], i32),
+        "sw_set_mode": ([vp, i32], i32),
         "sw_phase_times": ([vp, vp, ctypes.POINTER(i64)], i32),
         "ccl_label": ([vp, vp, i32, i32, i32, vp], i32),
         "ccl_workspace_bytes": ([i32, i32], i64),
@@ -205,6 +207,10 @@ def sw_debug_dump(h, mask_out=None, labels_out=None):
 
 def sw_stream(h):
     return int(lib().sw_stream(h) or 0)
+
+
+def sw_set_mode(h, mode):
+    _check(lib().sw_set_mode(h, mode))
 
 
 def sw_set_timing(h, enable):

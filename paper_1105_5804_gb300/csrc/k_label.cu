@@ -18,9 +18,9 @@
 //                 compact seam record.
 //  k_merge        one thread per bond leaving a tile (the periodic wrap
 //                 included, Sec. II.C): union of the two tile roots on the
-//                 global label array with atomicMin hooking.  Lanes that
-//                 carry the same root pair are collapsed with a warp match,
-//                 so consecutive seam bonds of one cluster cost one union.
+//                 global label array with atomicMin hooking.  A lane whose
+//                 root pair equals its left neighbour's skips the union, so
+//                 consecutive seam bonds of one cluster cost one union.
 //  k_root_compress  for every tile root: label = final root (pointer
 //                 jumping).  Because hooks always go to the smaller index,
 //                 the final root is the cluster's minimum site index.  In a
@@ -28,52 +28,25 @@
 //                 cluster's new state here (Sec. II.D), keyed by the root.
 //  k_site_compress  label[i] = label[label[i]] for every site (stand-alone
 //                 labeling only: leaves every label canonical).
-#include <climits>
-
-#include "swccl_device.cuh"
+#include "tile_engine.cuh"
 
 namespace swccl {
 
-namespace {
-constexpr int TILE_SITES = TILE_H * TILE_W;
-constexpr unsigned FULL = 0xFFFFFFFFu;
-}  // namespace
 
-// Local labeling of one tile (TILE_H x TILE_W sites, one warp per 32-column
-// strip).
-//  1. the tile's bond bits are copied to shared memory as they are packed in
-//     the mask, one 64-bit word (32 sites x {east, north}) per row and strip;
-//     bits of sites outside the grid and the east bond of the tile's last
-//     column are cleared;
-//  2. warp c sweeps its strip from row 0 upwards with the labels of the row
-//     below in registers.  A row is cut into runs of east-joined sites with
-//     one ballot.  A run reached from below through north bonds takes the
-//     label of its leftmost such site (one shuffle); a run nothing reaches
-//     gets a fresh label, the index of its first site (a union-find node).
-//     A lane reached from below by a label other than its run's appends the
-//     pair to its warp's list: no union-find work happens inside the sweep;
-//  3. the east bonds between strips and all listed pairs are joined by all
-//     threads at once with the shared-memory union-find (hooks larger roots
-//     under smaller ones); hooked roots are logged;
-//  4. logged roots resolve their final roots; every site's label is a node,
-//     so its root is par[par[site]].  The root is the smallest index of the
-//     tile component: the component's smallest site starts a run nothing
-//     reaches from below, so it is a node, and a smaller root never hooks
-//     under a larger one.  Its global index is therefore the minimum site
-//     index of the tile component.  Roots are listed per tile.
-//  5. the labels and outgoing bond bits of the four tile edges go to the
-//     tile's seam record.
+// Local labeling of one tile for the stand-alone labeling path: the tile's
+// bond bits are copied from the packed mask into shared memory (bits of
+// sites outside the grid and the east bond of the tile's last column
+// cleared), the engine of tile_engine.cuh labels the tile, and the kernel
+// writes every site's label (global index of its tile root, the minimum
+// site index of its tile component), the tile's root list, and the seam
+// record (labels and outgoing bond bits of the four tile edges).
 __global__ void __launch_bounds__(LABEL_THREADS)
 k_tile_label(const uint8_t* __restrict__ mask, int32_t* __restrict__ labels, Grid g,
              LabelScratch s) {
-  constexpr int STRIPS = TILE_W / 32;
-  constexpr int PAIR_CAP = TILE_SITES / STRIPS;   // per warp: (TILE_H - 1) * 32 pairs at most
-  static_assert((TILE_H - 1) * 32 <= PAIR_CAP, "pair list capacity");
-  __shared__ int par[TILE_SITES];
-  __shared__ unsigned long long mb[TILE_H * STRIPS];
-  __shared__ int warp_count[STRIPS];
-  __shared__ int warp_roots[LABEL_THREADS / 32];
-  __shared__ int n_hooked;
+  __shared__ TileSmem sm;
+  int* par = sm.par;
+  unsigned long long* mb = sm.mb;
+  int* warp_roots = sm.warp_roots;
 
   const int t = blockIdx.x;
   const int ty = t / g.tiles_x, tx = t - ty * g.tiles_x;
@@ -83,7 +56,7 @@ k_tile_label(const uint8_t* __restrict__ mask, int32_t* __restrict__ labels, Gri
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int32_t* slot = s.roots + (int64_t)t * TILE_SITES;     // pair lists, later the root list
   int32_t* hook_log = s.work + (int64_t)t * TILE_SITES;
-  if (threadIdx.x == 0) n_hooked = 0;
+  if (threadIdx.x == 0) sm.n_hooked = 0;
 
   // 1. bond bits
   for (int k = threadIdx.x; k < TILE_H * STRIPS; k += LABEL_THREADS) {
@@ -104,80 +77,8 @@ k_tile_label(const uint8_t* __restrict__ mask, int32_t* __restrict__ labels, Gri
   }
   __syncthreads();
 
-  // 2. strip sweep
-  {
-    const int col = warp * 32 + lane;
-    const unsigned below_lanes = (1u << lane) - 1u;
-    int32_t* pairs = slot + warp * PAIR_CAP;
-    int n_pairs = 0;
-    int lab_below = 0;
-    bool up_open = false;       // north bond from the site below into this lane's site
-    for (int ly = 0; ly < h; ++ly) {
-      const uint32_t b = (uint32_t)(mb[ly * STRIPS + warp] >> (2 * lane)) & 3u;
-      const uint32_t east = __ballot_sync(FULL, b & 1u) & 0x7FFFFFFFu;   // runs stay inside the strip
-      const uint32_t upb = __ballot_sync(FULL, up_open);
-      const uint32_t breaks = ~east & below_lanes;
-      const int start = breaks ? 32 - __clz(breaks) : 0;
-      const int end = lane + __ffs(~east >> lane) - 1;
-      const uint32_t run = ((2u << end) - 1u) & ~((1u << start) - 1u);
-      const uint32_t reach = upb & run;
-      const int first = reach ? __ffs(reach) - 1 : lane;
-      const int from_below = __shfl_sync(FULL, lab_below, first);
-      const int label = reach ? from_below : ly * TILE_W + warp * 32 + start;
-      par[ly * TILE_W + col] = label;
-      const int lab_left = __shfl_up_sync(FULL, lab_below, 1);
-      const bool dup = lane > start && ((upb >> (lane - 1)) & 1u) && lab_left == lab_below;
-      const bool pair = up_open && lab_below != label && !dup;
-      const uint32_t pm = __ballot_sync(FULL, pair);
-      if (pair) pairs[n_pairs + __popc(pm & below_lanes)] = (lab_below << 16) | label;
-      n_pairs += __popc(pm);
-      lab_below = label;
-      up_open = (b & 2u) != 0;
-    }
-    if (lane == 0) warp_count[warp] = n_pairs;
-  }
-  __syncthreads();
-
-  // 3. joins: east bonds between strips, then the listed pairs
-  {
-    int total = 0;
-#pragma unroll
-    for (int k = 0; k < STRIPS; ++k) total += warp_count[k];
-    constexpr int SEAMS = TILE_H * (STRIPS - 1);
-    for (int k = threadIdx.x; k < SEAMS + total; k += LABEL_THREADS) {
-      int a, b;
-      if (k < SEAMS) {
-        const int ly = k / (STRIPS - 1), c = k - ly * (STRIPS - 1);
-        if (ly >= h) continue;
-        if (!((mb[ly * STRIPS + c] >> 62) & 1ull)) continue;
-        if (ly > 0) {
-          const unsigned long long lo = mb[(ly - 1) * STRIPS + c], hi = mb[(ly - 1) * STRIPS + c + 1];
-          if (((lo >> 62) & 1ull) && ((lo >> 63) & 1ull) && ((hi >> 1) & 1ull)) continue;   // joined below
-        }
-        a = ly * TILE_W + c * 32 + 31;
-        b = a + 1;
-      } else {
-        int j = k - SEAMS, wsel = 0;
-        while (j >= warp_count[wsel]) j -= warp_count[wsel++];
-        const int v = slot[wsel * PAIR_CAP + j];
-        a = v >> 16;
-        b = v & 0xFFFF;
-      }
-      sm_union_log(par, a, b, TILE_SITES, s.err, hook_log, &n_hooked, TILE_SITES);
-    }
-  }
-  __syncthreads();
-
-  // 4a. hooked roots resolve their final roots (every other node is a root)
-  {
-    const int nh = min(n_hooked, TILE_SITES);
-    for (int k = threadIdx.x; k < nh; k += LABEL_THREADS) {
-      const int x = hook_log[k];
-      const int r = sm_find(par, x, TILE_SITES, s.err);
-      atomicMin(&par[x], r);
-    }
-  }
-  __syncthreads();
+  // 2-4a. label the tile
+  tile_engine(sm, h, w, slot, hook_log, s.err);
 
   // 4b. every site's root; global labels; root list
   constexpr int PER_T = TILE_SITES / LABEL_THREADS;
@@ -291,8 +192,9 @@ k_merge(int32_t* __restrict__ labels, Grid g, LabelScratch s, int limit) {
   valid = valid && a != b;
   const unsigned long long key =
       valid ? ((unsigned long long)(unsigned)min(a, b) << 32) | (unsigned)max(a, b) : ~0ull;
-  const unsigned same = __match_any_sync(FULL, key);
-  const bool leader = (__ffs(same) - 1) == (int)(threadIdx.x & 31);
+  // consecutive seam bonds usually join the same two roots: one union per run
+  const unsigned long long prev = __shfl_up_sync(FULL, key, 1);
+  const bool leader = (threadIdx.x & 31) == 0 || prev != key;
   if (valid && leader) g_union(labels, a, b, limit, s.err);
 }
 

@@ -76,10 +76,15 @@ struct sw_handle {
   SwCtl* ctl = nullptr;
   int* chk = nullptr;
   int64_t* obs = nullptr;
+  uint16_t* lroot = nullptr;   // fused mode: tile root of every site (local index)
+  int mode = SW_MODE_FUSED;
+  bool final_obs_pending = false;   // fused mode: observables of the last sweep not yet counted
   uint64_t sweeps = 0;     // sweeps enqueued
   uint64_t obs_read = 0;   // next sweep whose observables are unread
-  cudaGraph_t graph = nullptr;
+  cudaGraph_t graph = nullptr;        // one staged sweep
   cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph_fused = nullptr;  // one fused sweep
+  cudaGraphExec_t exec_fused = nullptr;
   bool timing = false;
   bool dump_valid = false;  // mask/labels hold the last sweep's result
   std::vector<cudaEvent_t> ev_pending;   // SW_N_PHASES + 1 events per timed sweep
@@ -93,6 +98,8 @@ void free_handle(sw_handle* h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->exec) cudaGraphExecDestroy(h->exec);
   if (h->graph) cudaGraphDestroy(h->graph);
+  if (h->exec_fused) cudaGraphExecDestroy(h->exec_fused);
+  if (h->graph_fused) cudaGraphDestroy(h->graph_fused);
   for (auto e : h->ev_pending) cudaEventDestroy(e);
   for (auto e : h->ev_free) cudaEventDestroy(e);
   cudaFree(h->spins);
@@ -102,6 +109,7 @@ void free_handle(sw_handle* h) {
   cudaFree(h->ctl);
   cudaFree(h->chk);
   cudaFree(h->obs);
+  cudaFree(h->lroot);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -123,6 +131,33 @@ cudaError_t enqueue_sweep(sw_handle* h, cudaEvent_t* ev) {
   if ((e = launch_flip(h->spins, h->labels, h->L, h->q, h->ctl, h->obs, OBS_CAP, st))) return e;
   if (ev && (e = cudaEventRecord(ev[5], st)) != cudaSuccess) return e;
   return launch_advance(h->ctl, st);
+}
+
+// Enqueue one fused sweep: draw + label, merge, flip, advance.  With timing
+// events the activation and root phases are recorded as empty.
+cudaError_t enqueue_sweep_fused(sw_handle* h, cudaEvent_t* ev) {
+  cudaError_t e;
+  const cudaStream_t st = h->stream;
+  if (ev && ((e = cudaEventRecord(ev[0], st)) != cudaSuccess || (e = cudaEventRecord(ev[1], st)) != cudaSuccess))
+    return e;
+  if ((e = launch_sw_label(h->spins, h->lroot, h->labels, h->grid, h->ls, h->q, h->T, h->seed, h->ctl, h->obs,
+                           OBS_CAP, st)))
+    return e;
+  if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
+  if ((e = launch_merge(h->labels, h->grid, h->ls, st))) return e;
+  if (ev && ((e = cudaEventRecord(ev[3], st)) != cudaSuccess || (e = cudaEventRecord(ev[4], st)) != cudaSuccess))
+    return e;
+  if ((e = launch_sw_flip(h->spins, h->lroot, h->labels, h->grid, h->ls, h->q, h->seed, h->ctl, st))) return e;
+  if (ev && (e = cudaEventRecord(ev[5], st)) != cudaSuccess) return e;
+  return launch_advance_fused(h->ctl, h->obs, OBS_CAP, h->q, st);
+}
+
+// Fused mode counts a sweep's observables in the next sweep's first kernel;
+// before the chain is read or changed, count the last sweep's here.
+cudaError_t finish_observables(sw_handle* h) {
+  if (!h->final_obs_pending) return cudaSuccess;
+  h->final_obs_pending = false;
+  return launch_observe(h->spins, h->L, h->q, h->ctl, h->obs, OBS_CAP, h->stream);
 }
 
 int check_device_status(sw_handle* h) {
@@ -204,9 +239,14 @@ sw_handle* sw_create_threshold(int L, int q, uint64_t T, uint64_t seed, int hot_
   if ((e = cudaMalloc(&h->ctl, sizeof(SwCtl)))) return bad(e, "control block");
   if ((e = cudaMalloc(&h->chk, sizeof(int)))) return bad(e, "check word");
   if ((e = cudaMalloc(&h->obs, (int64_t)OBS_CAP * (q + 1) * 8))) return bad(e, "observable ring");
+  if ((e = cudaMalloc(&h->lroot, (N * 2 + 15) & ~15LL))) return bad(e, "tile roots");
   h->ls = carve_label_scratch(h->grid, h->scratch,
                               reinterpret_cast<int*>(reinterpret_cast<char*>(h->ctl) + offsetof(SwCtl, err)));
-  if ((e = cudaMemsetAsync(h->ctl, 0, sizeof(SwCtl), h->stream))) return bad(e, "memset");
+  {
+    static const SwCtl init_ctl = {0ull, -1ll, 0, 0};
+    if ((e = cudaMemcpyAsync(h->ctl, &init_ctl, sizeof(SwCtl), cudaMemcpyHostToDevice, h->stream)))
+      return bad(e, "control block");
+  }
   if ((e = cudaMemsetAsync(h->obs, 0, (int64_t)OBS_CAP * (q + 1) * 8, h->stream))) return bad(e, "memset");
   if ((e = launch_init_spins(h->spins, L, q, seed, hot_start, h->stream))) return bad(e, "init spins");
   if ((e = cudaStreamSynchronize(h->stream))) return bad(e, "sync");
@@ -235,6 +275,9 @@ int sw_destroy(sw_handle* h) {
 int sw_sweep(sw_handle* h, int n) {
   if (!h) return fail(SW_ERR_ARG, "sw_sweep: null handle");
   if (n < 0) return fail(SW_ERR_ARG, "sw_sweep: n must be >= 0");
+  if (n == 0) return SW_OK;
+  const bool fused = h->mode == SW_MODE_FUSED;
+  auto enqueue = fused ? enqueue_sweep_fused : enqueue_sweep;
   if (h->timing) {
     for (int k = 0; k < n; ++k) {
       cudaEvent_t ev[SW_N_PHASES + 1];
@@ -247,27 +290,45 @@ int sw_sweep(sw_handle* h, int n) {
         }
         h->ev_pending.push_back(e);
       }
-      CK(enqueue_sweep(h, ev));
+      CK(enqueue(h, ev));
       h->sweeps++;
-      h->dump_valid = true;
     }
-    return SW_OK;
+  } else {
+    cudaGraph_t& graph = fused ? h->graph_fused : h->graph;
+    cudaGraphExec_t& exec = fused ? h->exec_fused : h->exec;
+    if (!exec) {
+      CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = enqueue(h, nullptr);
+      cudaGraph_t gr = nullptr;
+      cudaError_t e2 = cudaStreamEndCapture(h->stream, &gr);
+      if (e != cudaSuccess) { if (gr) cudaGraphDestroy(gr); return cuda_fail(e, "capture of one sweep"); }
+      if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+      graph = gr;
+      CK(cudaGraphInstantiate(&exec, graph, 0));
+    }
+    for (int k = 0; k < n; ++k) {
+      CK(cudaGraphLaunch(exec, h->stream));
+      h->sweeps++;
+    }
   }
-  if (!h->exec) {
-    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = enqueue_sweep(h, nullptr);
-    cudaGraph_t gr = nullptr;
-    cudaError_t e2 = cudaStreamEndCapture(h->stream, &gr);
-    if (e != cudaSuccess) { if (gr) cudaGraphDestroy(gr); return cuda_fail(e, "capture of one sweep"); }
-    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
-    h->graph = gr;
-    CK(cudaGraphInstantiate(&h->exec, h->graph, 0));
+  h->dump_valid = !fused;
+  h->final_obs_pending = fused;
+  return SW_OK;
+}
+
+int sw_set_mode(sw_handle* h, int mode) {
+  if (!h || (mode != SW_MODE_STAGED && mode != SW_MODE_FUSED)) return fail(SW_ERR_ARG, "sw_set_mode: bad arguments");
+  if (mode == h->mode) return SW_OK;
+  if (mode == SW_MODE_STAGED) {
+    CK(finish_observables(h));
+  } else {
+    // the staged flip already counted the last sweep's observables
+    const long long done = (long long)h->sweeps - 1;
+    CK(cudaMemcpyAsync(reinterpret_cast<char*>(h->ctl) + offsetof(SwCtl, obs_done), &done, sizeof(done),
+                       cudaMemcpyHostToDevice, h->stream));
   }
-  for (int k = 0; k < n; ++k) {
-    CK(cudaGraphLaunch(h->exec, h->stream));
-    h->sweeps++;
-    h->dump_valid = true;
-  }
+  CK(cudaStreamSynchronize(h->stream));
+  h->mode = mode;
   return SW_OK;
 }
 
@@ -279,6 +340,7 @@ int sw_sync(sw_handle* h) {
 int sw_observables(sw_handle* h, int64_t* out, int max_sweeps, int* n_written) {
   if (!h || (!out && max_sweeps > 0) || max_sweeps < 0) return fail(SW_ERR_ARG, "sw_observables: bad arguments");
   if (n_written) *n_written = 0;
+  CK(finish_observables(h));
   int rc = check_device_status(h);
   if (rc) return rc;
   if (h->sweeps - h->obs_read > (uint64_t)OBS_CAP) h->obs_read = h->sweeps - OBS_CAP;
@@ -312,6 +374,7 @@ int sw_set_spins(sw_handle* h, const int8_t* src, int is_device) {
   // Host input is staged in the label buffer (4N bytes, rewritten by the
   // next sweep) and validated there by a kernel; device input is validated
   // in place.  The spins change only if every value is in [0, q).
+  CK(finish_observables(h));
   const int8_t* dsrc = src;
   if (!is_device) {
     int8_t* staging = reinterpret_cast<int8_t*>(h->labels);
@@ -333,7 +396,9 @@ int sw_set_spins(sw_handle* h, const int8_t* src, int is_device) {
 int sw_debug_dump(sw_handle* h, uint8_t* mask_out, int32_t* labels_out, int is_device) {
   if (!h) return fail(SW_ERR_ARG, "sw_debug_dump: null handle");
   if (!h->dump_valid)
-    return fail(SW_ERR_STATE, "sw_debug_dump: no sweep has run since creation or the last sw_set_spins");
+    return fail(SW_ERR_STATE,
+                "sw_debug_dump: the last sweep did not run in SW_MODE_STAGED, or no sweep has run since "
+                "creation or the last sw_set_spins");
   const int64_t N = (int64_t)h->L * h->L;
   const cudaMemcpyKind kind = is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (labels_out) {

@@ -65,6 +65,7 @@ struct LabelScratch {
 // Control block of a Swendsen-Wang chain, in device memory.
 struct SwCtl {
   unsigned long long sweep;  // index of the sweep being computed
+  long long obs_done;        // fused mode: last sweep whose observables k_observe completed (-1: none)
   int err;                   // first device-side failure (SW_ERR_*)
   int pad;
 };
@@ -98,6 +99,16 @@ cudaError_t launch_site_compress(int32_t* labels, int64_t n_sites, cudaStream_t 
 cudaError_t launch_flip(int8_t* spins, const int32_t* labels, int L, int q, const SwCtl* ctl,
                         int64_t* obs_ring, int obs_cap, cudaStream_t st);
 cudaError_t launch_advance(SwCtl* ctl, cudaStream_t st);
+
+// Fused sweep (activation inside labeling; no mask or int32 labels in HBM).
+cudaError_t launch_sw_label(const int8_t* spins, uint16_t* lroot, int32_t* gpar, const Grid& g,
+                            const LabelScratch& s, int q, uint64_t T, uint64_t seed, const SwCtl* ctl,
+                            int64_t* obs, int obs_cap, cudaStream_t st);
+cudaError_t launch_sw_flip(int8_t* spins, const uint16_t* lroot, int32_t* gpar, const Grid& g,
+                           const LabelScratch& s, int q, uint64_t seed, const SwCtl* ctl, cudaStream_t st);
+cudaError_t launch_observe(const int8_t* spins, int L, int q, SwCtl* ctl, int64_t* obs, int obs_cap,
+                           cudaStream_t st);
+cudaError_t launch_advance_fused(SwCtl* ctl, int64_t* obs, int obs_cap, int q, cudaStream_t st);
 
 // Host helpers of the C ABI: set this thread's sw_last_error() message and
 // return `code`; device address of the stand-alone labeling status word on

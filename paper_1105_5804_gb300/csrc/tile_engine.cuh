@@ -1,0 +1,140 @@
+// tile_engine.cuh -- the tile-local labeling engine shared by the
+// stand-alone labeling kernel (bond mask in memory) and the fused
+// Swendsen-Wang kernel (bonds drawn on the fly).
+//
+// Input: the tile's bond bits in shared memory, one 64-bit word per row and
+// 32-column strip (bit 2i: east bond of site i, bit 2i+1: north bond), with
+// bits of sites outside the grid and the east bond of the tile's last column
+// cleared.  Output: par[] such that every site's tile root is
+// par[par[site]], the root being the smallest local index of the site's
+// tile component.
+//
+//  1. warp c sweeps strip c from row 0 upwards with the labels of the row
+//     below in registers.  A row is cut into runs of east-joined sites with
+//     one ballot.  A run reached from below through north bonds takes the
+//     label of its leftmost such site (one shuffle); a run nothing reaches
+//     gets a fresh label, the index of its first site (a union-find node).
+//     A lane reached from below by a label other than its run's appends the
+//     pair to its warp's list: no union-find work happens inside the sweep;
+//  2. the east bonds between strips and all listed pairs are joined by all
+//     threads at once with the shared-memory union-find (larger root hooked
+//     under the smaller); hooked roots are logged;
+//  3. logged roots resolve their final roots, so every node points at its
+//     root and every site's label (a node) is one step from it.
+// The root is the smallest index of the tile component: the component's
+// smallest site starts a run nothing reaches from below, so it is a node,
+// and a smaller root never hooks under a larger one.
+#pragma once
+#include <climits>
+
+#include "swccl_device.cuh"
+
+namespace swccl {
+
+constexpr int TILE_SITES = TILE_H * TILE_W;
+constexpr int STRIPS = TILE_W / 32;
+constexpr int PAIR_CAP = TILE_SITES / STRIPS;   // per warp: (TILE_H - 1) * 32 pairs at most
+static_assert((TILE_H - 1) * 32 <= PAIR_CAP, "pair list capacity");
+static_assert(LABEL_THREADS == TILE_W, "one warp per 32-column strip");
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+struct TileSmem {
+  int par[TILE_SITES];
+  unsigned long long mb[TILE_H * STRIPS];
+  int warp_count[STRIPS];
+  int warp_roots[LABEL_THREADS / 32];
+  int n_hooked;
+};
+
+// Global index of local index r of the tile at (y0, x0) of a W-wide grid.
+__device__ __forceinline__ int tile_global(int r, int y0, int x0, int W) {
+  return (y0 + (r >> TILE_W_LOG2)) * W + x0 + (r & (TILE_W - 1));
+}
+
+// Runs the engine; sm.mb must be filled and sm.n_hooked zero, followed by a
+// __syncthreads().  `slot` (TILE_SITES ints of global scratch) holds the
+// pair lists; `hook_log` (TILE_SITES ints) the hooked roots.  Ends with a
+// __syncthreads().
+__device__ __forceinline__ void tile_engine(TileSmem& sm, int h, int w, int32_t* slot, int32_t* hook_log,
+                                            int* err) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int* par = sm.par;
+  unsigned long long* mb = sm.mb;
+  int* warp_count = sm.warp_count;
+  // 1. strip sweep
+  {
+    const int col = warp * 32 + lane;
+    const unsigned below_lanes = (1u << lane) - 1u;
+    int32_t* pairs = slot + warp * PAIR_CAP;
+    int n_pairs = 0;
+    int lab_below = 0;
+    bool up_open = false;       // north bond from the site below into this lane's site
+    for (int ly = 0; ly < h; ++ly) {
+      const uint32_t b = (uint32_t)(mb[ly * STRIPS + warp] >> (2 * lane)) & 3u;
+      const uint32_t east = __ballot_sync(FULL, b & 1u) & 0x7FFFFFFFu;   // runs stay inside the strip
+      const uint32_t upb = __ballot_sync(FULL, up_open);
+      const uint32_t breaks = ~east & below_lanes;
+      const int start = breaks ? 32 - __clz(breaks) : 0;
+      const int end = lane + __ffs(~east >> lane) - 1;
+      const uint32_t run = ((2u << end) - 1u) & ~((1u << start) - 1u);
+      const uint32_t reach = upb & run;
+      const int first = reach ? __ffs(reach) - 1 : lane;
+      const int from_below = __shfl_sync(FULL, lab_below, first);
+      const int label = reach ? from_below : ly * TILE_W + warp * 32 + start;
+      par[ly * TILE_W + col] = label;
+      const int lab_left = __shfl_up_sync(FULL, lab_below, 1);
+      const bool dup = lane > start && ((upb >> (lane - 1)) & 1u) && lab_left == lab_below;
+      const bool pair = up_open && lab_below != label && !dup;
+      const uint32_t pm = __ballot_sync(FULL, pair);
+      if (pair) pairs[n_pairs + __popc(pm & below_lanes)] = (lab_below << 16) | label;
+      n_pairs += __popc(pm);
+      lab_below = label;
+      up_open = (b & 2u) != 0;
+    }
+    if (lane == 0) warp_count[warp] = n_pairs;
+  }
+  __syncthreads();
+
+  // 2. joins: east bonds between strips, then the listed pairs
+  {
+    int total = 0;
+#pragma unroll
+    for (int k = 0; k < STRIPS; ++k) total += warp_count[k];
+    constexpr int SEAMS = TILE_H * (STRIPS - 1);
+    for (int k = threadIdx.x; k < SEAMS + total; k += LABEL_THREADS) {
+      int a, b;
+      if (k < SEAMS) {
+        const int ly = k / (STRIPS - 1), c = k - ly * (STRIPS - 1);
+        if (ly >= h) continue;
+        if (!((mb[ly * STRIPS + c] >> 62) & 1ull)) continue;
+        if (ly > 0) {
+          const unsigned long long lo = mb[(ly - 1) * STRIPS + c], hi = mb[(ly - 1) * STRIPS + c + 1];
+          if (((lo >> 62) & 1ull) && ((lo >> 63) & 1ull) && ((hi >> 1) & 1ull)) continue;   // joined below
+        }
+        a = ly * TILE_W + c * 32 + 31;
+        b = a + 1;
+      } else {
+        int j = k - SEAMS, wsel = 0;
+        while (j >= warp_count[wsel]) j -= warp_count[wsel++];
+        const int v = slot[wsel * PAIR_CAP + j];
+        a = v >> 16;
+        b = v & 0xFFFF;
+      }
+      sm_union_log(par, a, b, TILE_SITES, err, hook_log, &sm.n_hooked, TILE_SITES);
+    }
+  }
+  __syncthreads();
+
+  // 3. hooked roots resolve their final roots (every other node is a root)
+  {
+    const int nh = min(sm.n_hooked, TILE_SITES);
+    for (int k = threadIdx.x; k < nh; k += LABEL_THREADS) {
+      const int x = hook_log[k];
+      const int r = sm_find(par, x, TILE_SITES, err);
+      atomicMin(&par[x], r);
+    }
+  }
+  __syncthreads();
+}
+
+}  // namespace swccl

@@ -25,8 +25,10 @@ KC = 0.5 * math.log(1.0 + math.sqrt(2.0))
 
 
 def _run_parity(L, q, T, seed, hot, n_sweeps, sweep_graph=True):
+    """Staged mode: every sweep's mask, labels, spins and observables."""
     h = sw.sw_create_threshold(L, q, T, seed, hot)
     try:
+        sw.sw_set_mode(h, sw.SW_MODE_STAGED)
         if not sweep_graph:
             sw.sw_set_timing(h, True)
         s = oracle.init_spins(L, q, seed, hot)
@@ -52,6 +54,7 @@ def test_ising_L64_cold_start_1000_sweeps_bit_exact():
     T = oracle.threshold(oracle.coupling_K(q, KC, 1.0, oracle.CONV_ISING))
     h = sw.sw_create_ex(L, q, KC, 1.0, sw.SW_CONV_ISING, seed, False)
     try:
+        sw.sw_set_mode(h, sw.SW_MODE_STAGED)
         s = oracle.init_spins(L, q, seed, False)
         gobs_all = []
         for k in range(1000):
@@ -172,6 +175,7 @@ def test_L16384_one_step_equivalence(q, beta, conv):
     T = oracle.threshold(oracle.coupling_K(q, beta, 1.0, conv))
     h = sw.sw_create_ex(L, q, beta, 1.0, conv, seed, True)
     try:
+        sw.sw_set_mode(h, sw.SW_MODE_STAGED)
         s = sw.sw_get_spins(h)
         assert np.array_equal(s[:1 << 16], oracle.init_spins(L, q, seed, True)[:1 << 16])
         samples = (0, 2) if q == 2 else (0,)
@@ -189,6 +193,122 @@ def test_L16384_one_step_equivalence(q, beta, conv):
             s_new, m, lab, obs = oracle.sweep(L, q, T, seed, k, s)
             assert np.array_equal(gm, m)
             assert np.array_equal(glab, lab)
+            assert np.array_equal(gs, s_new)
+            assert np.array_equal(gobs[-1], obs)
+            s = gs
+    finally:
+        sw.sw_destroy(h)
+
+
+# ---------------------------------------------------------------------------
+# Fused mode (default): bonds drawn inside the labeling kernel.  No mask or
+# labels exist to dump; spins and observables are compared every sweep.
+# ---------------------------------------------------------------------------
+def _run_fused(L, q, T, seed, hot, n_sweeps, per_call=1, timing=False):
+    h = sw.sw_create_threshold(L, q, T, seed, hot)
+    try:
+        if timing:
+            sw.sw_set_timing(h, True)
+        s = oracle.init_spins(L, q, seed, hot)
+        done = 0
+        while done < n_sweeps:
+            k = min(per_call, n_sweeps - done)
+            sw.sw_sweep(h, k)
+            s, obs = oracle.chain(L, q, T, seed, done, k, s)
+            assert np.array_equal(sw.sw_get_spins(h), s), ("spins", L, q, done)
+            assert np.array_equal(sw.sw_observables(h, 4096), obs), ("obs", L, q, done)
+            done += k
+        with pytest.raises(sw.SwcclError):
+            sw.sw_debug_dump(h)          # nothing to dump after a fused sweep
+    finally:
+        sw.sw_destroy(h)
+
+
+def test_fused_ising_L64_cold_start_1000_sweeps():
+    L, q, seed = 64, 2, 1
+    T = oracle.threshold(oracle.coupling_K(q, KC, 1.0, oracle.CONV_ISING))
+    _run_fused(L, q, T, seed, False, 1000, per_call=50)
+
+
+@pytest.mark.parametrize("L", [4, 8, 36, 100, 132, 196, 260, 292])
+@pytest.mark.parametrize("q", [2, 3, 4])
+def test_fused_small_lattices(L, q):
+    beta = math.log(1 + math.sqrt(q))
+    T = oracle.threshold(oracle.coupling_K(q, beta, 1.0, oracle.CONV_POTTS))
+    _run_fused(L, q, T, seed=2000 + L + q, hot=True, n_sweeps=8, per_call=3)
+
+
+@pytest.mark.parametrize("q", [5, 9, 127])
+def test_fused_many_states(q):
+    T = oracle.threshold(oracle.coupling_K(q, math.log(1 + math.sqrt(q)), 1.0, oracle.CONV_POTTS))
+    _run_fused(260, q, T, seed=8, hot=True, n_sweeps=5)
+
+
+@pytest.mark.parametrize("T", [0, 1, 1 << 31, (1 << 32) - 1, 1 << 32])
+def test_fused_degenerate_thresholds(T):
+    _run_fused(68, 2, T, seed=3, hot=True, n_sweeps=4)
+
+
+def test_fused_timed_mode_and_one_sweep_per_call():
+    T = oracle.threshold(oracle.coupling_K(2, KC, 1.0, oracle.CONV_ISING))
+    _run_fused(292, 2, T, seed=12, hot=True, n_sweeps=6, timing=True)
+
+
+def test_mode_switches_keep_the_chain():
+    """staged -> fused -> staged -> fused within one chain, with reads of the
+    observables at every switch and in between."""
+    L, q, seed = 260, 3, 44
+    T = oracle.threshold(oracle.coupling_K(q, math.log(1 + math.sqrt(3)), 1.0, oracle.CONV_POTTS))
+    h = sw.sw_create_threshold(L, q, T, seed, True)
+    try:
+        s = oracle.init_spins(L, q, seed, True)
+        done = 0
+        all_obs = []
+        for mode, n in [(sw.SW_MODE_STAGED, 3), (sw.SW_MODE_FUSED, 4), (sw.SW_MODE_STAGED, 2),
+                        (sw.SW_MODE_FUSED, 5), (sw.SW_MODE_FUSED, 1)]:
+            sw.sw_set_mode(h, mode)
+            sw.sw_sweep(h, n)
+            s, obs = oracle.chain(L, q, T, seed, done, n, s)
+            done += n
+            all_obs.append(obs)
+            assert np.array_equal(sw.sw_get_spins(h), s)
+        got = sw.sw_observables(h, 4096)
+        assert np.array_equal(got, np.concatenate(all_obs))
+        # set_spins after fused sweeps: the pending observables belong to the old spins
+        sw.sw_sweep(h, 2)
+        s, obs = oracle.chain(L, q, T, seed, done, 2, s)
+        done += 2
+        rng = np.random.default_rng(1)
+        new = rng.integers(0, q, L * L).astype(np.int8)
+        sw.sw_set_spins(h, new)
+        sw.sw_sweep(h, 1)
+        s2, obs2 = oracle.chain(L, q, T, seed, done, 1, new)
+        assert np.array_equal(sw.sw_observables(h, 4096), np.concatenate([obs, obs2]))
+        assert np.array_equal(sw.sw_get_spins(h), s2)
+    finally:
+        sw.sw_destroy(h)
+
+
+@pytest.mark.parametrize("q,beta,conv", [(2, KC, sw.SW_CONV_ISING), (4, math.log(3.0), sw.SW_CONV_POTTS)])
+def test_fused_L16384_one_step_equivalence(q, beta, conv):
+    """The benchmark's lattice and mode: L = 16384, hot start seed 7, fused
+    sweeps.  Sweep 0 is checked in full against the oracle stepping the
+    initial spins; after two more fused sweeps, sweep 3 is checked from the
+    GPU's pre-sweep spins."""
+    L, seed = 16384, 7
+    T = oracle.threshold(oracle.coupling_K(q, beta, 1.0, conv))
+    h = sw.sw_create_ex(L, q, beta, 1.0, conv, seed, True)
+    try:
+        s = sw.sw_get_spins(h)
+        for k in (0, 3):
+            if k > 0:
+                sw.sw_sweep(h, k - 1)
+                sw.sw_observables(h, 4096)
+                s = sw.sw_get_spins(h)
+            sw.sw_sweep(h, 1)
+            gs = sw.sw_get_spins(h)
+            gobs = sw.sw_observables(h, 4)
+            s_new, _, _, obs = oracle.sweep(L, q, T, seed, k, s)
             assert np.array_equal(gs, s_new)
             assert np.array_equal(gobs[-1], obs)
             s = gs
