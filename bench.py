@@ -29,9 +29,14 @@ L_BENCH, Q_BENCH, SEED_BENCH = 16384, 2, 7
 # self-labeling + sewing on a Tesla M2070, 3.573 ns per site and sweep (Table I)
 PAPER_SITE_UPDATES_PER_NS = 1.0 / 3.573
 WORKLOAD = "sw_ising_q2_L16384_beta_c_hot_start_seed7"
-# algorithmic bytes per site of the tile-labeling kernel: read the 2-bit mask
-# (0.25 B) and write one int32 label (4 B)
-TILE_LABEL_BYTES_PER_SITE = 4.25
+# Algorithmic HBM bytes per site of one fused sweep: k_sw_label reads the
+# int8 spins (1 B) and writes a 16-bit tile root (2 B); k_sw_flip reads the
+# root (2 B) and writes the spins (1 B).  Seam records and edge-root entries
+# (O(1/tile side)) are not counted.
+FUSED_SWEEP_BYTES_PER_SITE = 6.0
+# Philox4x32-10 calls per site made by k_sw_label: one call per pair of
+# x-adjacent sites (its four words are the pair's east and north bonds)
+LABEL_PHILOX_CALLS_PER_SITE = 0.5
 
 
 def _peaks():
@@ -100,6 +105,24 @@ class ClockSampler:
         sm.sort()
         return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def max_over_ranks(x, device=None):
+    """Largest value of x over all ranks (plain x without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    if device is None:
+        device = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_seed(rank):
+    """Seed of the independent replica run by a rank."""
+    return SEED_BENCH + rank
 
 
 def _dist():
@@ -205,6 +228,28 @@ def ccl_secondary(torch, sw, n_seeds=20):
             "l2": "flushed (256 MiB write) between labels"}
 
 
+def philox_ceiling(torch, sw, reps=3):
+    """Measured integer-ALU ceiling: Philox4x32-10 calls per second of a
+    kernel that does nothing else, 8 CTAs x 256 threads per SM on every SM."""
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    blocks = sms * 8
+    calls = 4096
+    sink = torch.empty(blocks * 256, dtype=torch.int32, device="cuda")
+    st = torch.cuda.current_stream()
+    sw.sw_probe_philox(calls, blocks, sink)
+    best = None
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        sw.sw_probe_philox(calls, blocks, sink)
+        b.record(st)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        best = ms if best is None else min(best, ms)
+    return blocks * 256 * calls / (best * 1e-3)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -218,7 +263,7 @@ def run_ours(args):
 
     L, q = args.L, Q_BENCH
     N = L * L
-    seed = SEED_BENCH + rank
+    seed = replica_seed(rank)
     h = sw.sw_create_ex(L, q, KC_ISING, 1.0, sw.SW_CONV_ISING, seed, True)
     stream = torch.cuda.ExternalStream(sw.sw_stream(h))
 
@@ -253,14 +298,10 @@ def run_ours(args):
     t1 = time.time()
     barrier()
     clk = clocks.stop(t0, t1)
-    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(ev0.elapsed_time(ev1))
     phases, n_timed = sw.sw_phase_times(h)
     sw.sw_set_timing(h, False)
     obs = sw.sw_observables(h, 4096)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
     value = world * N * args.steps / (ms * 1e6)
 
     # end to end through the C ABI with host buffers: upload spins, one sweep,
@@ -277,11 +318,7 @@ def run_ours(args):
         sw.sw_sweep(h, 1)
         o = sw.sw_observables(h, 1)
         sw.sw_get_spins(h, host_out.numpy())
-    te = time.perf_counter() - te0
-    if world > 1:
-        t = torch.tensor([te], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        te = float(t.item())
+    te = max_over_ranks(time.perf_counter() - te0)
     e2e_value = world * N * e2e_steps / (te * 1e9) if e2e_steps else None
 
     secondary = {}
@@ -304,9 +341,13 @@ def run_ours(args):
 
     if rank != 0:
         return
-    peak, peak_kind = _peaks()
-    local_ms = phases["local"] / max(n_timed, 1)
-    achieved = TILE_LABEL_BYTES_PER_SITE * N / (local_ms * 1e-3) / 1e9
+    peak_hbm, peak_kind = _peaks()
+    ms_sweep = ms / args.steps
+    per = {k: v / max(n_timed, 1) for k, v in phases.items()}
+    label_ms = per["local"]
+    philox_peak = philox_ceiling(torch, sw)
+    philox_achieved = LABEL_PHILOX_CALLS_PER_SITE * N / (label_ms * 1e-3)
+    hbm_achieved = FUSED_SWEEP_BYTES_PER_SITE * N / (ms_sweep * 1e-3) / 1e9
     mean_n_eq = float(obs[:, 0].mean()) if len(obs) else None
     line = {
         "metric": "SW site-updates/ns", "value": value, "unit": "site-updates/ns", "n_gpus": world,
@@ -318,16 +359,24 @@ def run_ours(args):
                    "start": "hot", "seed": SEED_BENCH, "replicas": world, "parallelism": "replicas",
                    "l2": "inputs larger than L2 (int32 labels 1 GiB, spins 256 MiB per replica)"},
         "clocks": clk,
-        "gpu_launches": 6 * args.steps,
+        "gpu_launches": 4 * args.steps,
         "e2e": {"value": e2e_value, "unit": "site-updates/ns", "h2d_bytes_per_step": N,
                 "d2h_bytes_per_step": N + 8 * (q + 1), "steps": e2e_steps,
                 "path": "sw_set_spins(host) + sw_sweep(1) + sw_observables + sw_get_spins(host), pinned buffers"},
-        "roofline": {"bound": "hbm", "kernel": "k_tile_label", "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                     "peak_kind": peak_kind,
-                     "bytes_model": "%.2f B/site (mask 0.25 read + int32 label 4 write) x %d sites per launch"
-                                    % (TILE_LABEL_BYTES_PER_SITE, N)},
-        "phase_ms_per_sweep": {k: v / max(n_timed, 1) for k, v in phases.items()},
+        "roofline": {"bound": "alu", "kernel": "k_sw_label", "achieved": philox_achieved / 1e9,
+                     "peak": philox_peak / 1e9, "unit": "Gcall/s (Philox4x32-10)",
+                     "frac": philox_achieved / philox_peak, "traffic": None,
+                     "peak_kind": "measured in this run: Philox-only kernel, 8 CTAs x 256 threads per SM",
+                     "work_model": "%.1f Philox calls/site x %d sites per launch; the kernel also labels its "
+                                   "tile, which shares the integer pipes" % (LABEL_PHILOX_CALLS_PER_SITE, N),
+                     "ms_per_launch": label_ms},
+        "hbm_view": {"bytes_per_site": FUSED_SWEEP_BYTES_PER_SITE, "achieved": hbm_achieved, "peak": peak_hbm,
+                     "unit": "GB/s", "frac": hbm_achieved / peak_hbm, "peak_kind": peak_kind,
+                     "model": "whole fused sweep: spins read 1 B + 16-bit roots written 2 B (k_sw_label), "
+                              "roots read 2 B + spins written 1 B (k_sw_flip)"},
+        "phase_ms_per_sweep": per,
+        "kernels_per_phase": {"local": "k_sw_label (bond draws + tile labeling)", "merge": "k_merge",
+                              "flip": "k_sw_flip", "activate": "(fused into local)", "roots": "(fused into flip)"},
         "mean_n_eq_per_site": mean_n_eq / N if mean_n_eq else None,
         "secondary": secondary,
     }

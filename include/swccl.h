@@ -245,6 +245,18 @@ int ccl_label_noalloc(const uint8_t* bond_mask, int32_t* labels, int H, int W, i
  * recorded by ccl_* kernels since the last call (SW_OK if none); clears it. */
 int ccl_status(void);
 
+/* ------------------------------------------------------------------------ */
+/* Measurement helper (not part of the method)                               */
+/* ------------------------------------------------------------------------ */
+
+/* Enqueue a kernel of `blocks` x 256 threads that only evaluates
+ * Philox4x32-10: every thread makes calls_per_thread (a positive multiple of
+ * 4) independent calls and stores one folded word to sink[thread]
+ * (device, blocks*256 uint32).  Timing it gives the integer-ALU ceiling of
+ * the bond draws (Philox4x32-10 calls per second), the bound of the
+ * activation kernels. */
+int sw_probe_philox(int64_t calls_per_thread, int blocks, uint32_t* sink, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -14,7 +14,7 @@ from ._lib import (  # noqa: F401
     sw_sweep, sw_sync, sw_observables, sw_get_spins, sw_set_spins, sw_debug_dump, sw_get_info,
     sw_stream, sw_set_timing, sw_phase_times, sw_set_mode,
     ccl_label, ccl_workspace_bytes, ccl_label_ws, ccl_bonds_from_pixels, ccl_perc_mask, ccl_status,
-    ccl_label_noalloc, CCL_NOALLOC_SCRATCH_BYTES,
+    ccl_label_noalloc, CCL_NOALLOC_SCRATCH_BYTES, sw_probe_philox,
 )
 
 

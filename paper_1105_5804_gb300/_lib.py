@@ -64,6 +64,7 @@ def lib():
         "ccl_perc_mask": ([u64, vp, i32, i32, vp], i32),
         "ccl_label_noalloc": ([vp, vp, i32, i32, i32, vp], i32),
         "ccl_status": ([], i32),
+        "sw_probe_philox": ([i64, i32, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -278,6 +279,13 @@ def ccl_label_noalloc(bond_mask, labels, H, W, periodic, stream=None):
                                    _dev(labels, torch.int32, N, "labels"), H, W, 1 if periodic else 0,
                                    _stream(stream)))
     return labels
+
+
+def sw_probe_philox(calls_per_thread, blocks, sink, stream=None):
+    """Enqueue the Philox-only throughput kernel (measurement helper)."""
+    import torch
+    _check(lib().sw_probe_philox(calls_per_thread, blocks, _dev(sink, torch.int32, blocks * 256, "sink"),
+                                 _stream(stream)))
 
 
 def ccl_status():

@@ -1,0 +1,392 @@
+// fused_tile.cuh -- per-tile bodies of the fused Swendsen-Wang sweep, shared
+// by the single-lattice kernels (k_fused.cu) and the batched / persistent
+// kernels over many lattices (k_batch.cu).  Description of the steps in
+// k_fused.cu.
+#pragma once
+#include "tile_engine.cuh"
+
+namespace swccl {
+
+// One lattice as the fused kernels see it.
+struct SwRep {
+  int8_t* spins;      // L*L int8
+  uint16_t* lroot;    // L*L tile roots (local index)
+  int32_t* gpar;      // L*L parent entries (only edge roots are used)
+  int64_t* obs;       // observable ring: obs_cap x (1 + q)
+  LabelScratch s;     // per-tile pair lists, hook logs, seam records, status word
+  Grid g;             // L x L, periodic
+  uint64_t T, seed;
+  int q;
+  int tile0;          // first global tile of this lattice in a batch
+};
+
+namespace fused {
+
+// Four byte lanes of a and b compared: bit k of the result is set iff byte k
+// of a equals byte k of b.
+__device__ __forceinline__ uint32_t eq4(uint32_t a, uint32_t b) {
+  const uint32_t m = __vcmpeq4(a, b);               // 0xFF per equal byte
+  return ((m & 0x08040201u) * 0x01010101u) >> 24;   // gather one bit per byte
+}
+
+// Bonds (and observable counts) of 32 consecutive sites of one row.
+struct RowBonds {
+  unsigned long long word;  // bit 2i east bond, 2i+1 north bond (rule of Eq. 7)
+  uint32_t eq_e, eq_n;      // site i equals its east / north neighbour
+};
+
+__device__ __forceinline__ RowBonds row_bonds(const int8_t* __restrict__ spins, int L, int y, int x, int nvalid,
+                                              uint64_t T, uint32_t klo, uint32_t khi, uint32_t sw_lo,
+                                              uint32_t sw_hi) {
+  RowBonds rb{0ull, 0u, 0u};
+  const int yn = (y + 1 == L) ? 0 : y + 1;
+  const int64_t row = (int64_t)y * L, rown = (int64_t)yn * L;
+  uint32_t s[8], n[8];
+  const int nw = nvalid >> 2;   // whole 4-site words (L % 4 == 0)
+  if (nw == 8 && (L & 15) == 0) {
+    const uint4 a0 = *reinterpret_cast<const uint4*>(spins + row + x);
+    const uint4 a1 = *reinterpret_cast<const uint4*>(spins + row + x + 16);
+    const uint4 b0 = *reinterpret_cast<const uint4*>(spins + rown + x);
+    const uint4 b1 = *reinterpret_cast<const uint4*>(spins + rown + x + 16);
+    s[0] = a0.x; s[1] = a0.y; s[2] = a0.z; s[3] = a0.w; s[4] = a1.x; s[5] = a1.y; s[6] = a1.z; s[7] = a1.w;
+    n[0] = b0.x; n[1] = b0.y; n[2] = b0.z; n[3] = b0.w; n[4] = b1.x; n[5] = b1.y; n[6] = b1.z; n[7] = b1.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      s[k] = (k < nw) ? *reinterpret_cast<const uint32_t*>(spins + row + x + 4 * k) : 0u;
+      n[k] = (k < nw) ? *reinterpret_cast<const uint32_t*>(spins + rown + x + 4 * k) : 0u;
+    }
+  }
+  const int xe = (x + nvalid == L) ? 0 : x + nvalid;
+  const uint32_t east_byte = (uint32_t)(uint8_t)spins[row + xe];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if (k < nw) {
+      const uint32_t next = (k + 1 < nw) ? s[k + 1] : east_byte;
+      const uint32_t e = (s[k] >> 8) | (next << 24);
+      rb.eq_e |= eq4(s[k], e) << (4 * k);
+      rb.eq_n |= eq4(s[k], n[k]) << (4 * k);
+    }
+  }
+  const bool all_open = T >= (1ull << 32);
+  const uint32_t thr = (uint32_t)T;
+  const uint32_t eq = rb.eq_e | rb.eq_n;
+#pragma unroll
+  for (int i = 0; i < 32; i += 2) {
+    if (i >= nvalid) break;
+    const uint32_t need = (eq >> i) & 3u;
+    if (!need) continue;
+    const uint32_t e0 = (rb.eq_e >> i) & 1u, n0 = (rb.eq_n >> i) & 1u;
+    const uint32_t e1 = (rb.eq_e >> (i + 1)) & 1u, n1 = (rb.eq_n >> (i + 1)) & 1u;
+    uint32_t bits;
+    if (all_open) {
+      bits = e0 | (n0 << 1) | (e1 << 2) | (n1 << 3);
+    } else if (thr == 0) {
+      bits = 0;
+    } else {
+      const uint4 r = philox(make_uint4((uint32_t)((row + x + i) >> 1), sw_lo, sw_hi, TAG_BOND), klo, khi);
+      bits = (e0 & (r.x < thr)) | ((n0 & (r.y < thr)) << 1) | ((e1 & (r.z < thr)) << 2) | ((n1 & (r.w < thr)) << 3);
+    }
+    rb.word |= (unsigned long long)bits << (2 * i);
+  }
+  return rb;
+}
+
+// Number of sites in state k among the first nvalid bytes of s (k < q).
+__device__ __forceinline__ int count_state(const int8_t* __restrict__ p, int nvalid, int k) {
+  int c = 0;
+  for (int j = 0; j < nvalid; j += 4) c += __popc(eq4(*reinterpret_cast<const uint32_t*>(p + j), 0x01010101u * (uint32_t)k));
+  return c;
+}
+
+constexpr int QREG_MAX = 8;
+
+// Block-wide sums of n_eq and the state counts, added to the observable slot.
+template <int NTHREADS>
+__device__ __forceinline__ void add_observables(long long n_eq, const int* cnt, int q, int qreg, unsigned long long* slot,
+                                unsigned long long* red /* shared, (1 + qreg) * NTHREADS/32 */,
+                                int* hist /* shared, 128, already holds counts when qreg == 0 */) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = NTHREADS / 32;
+  unsigned long long v = (unsigned long long)n_eq;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+  if (lane == 0) red[warp] = v;
+#pragma unroll
+  for (int k = 0; k < QREG_MAX; ++k) {
+    if (k >= qreg) break;
+    unsigned long long c = (unsigned long long)cnt[k];
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(FULL, c, o);
+    if (lane == 0) red[(1 + k) * NW + warp] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x <= qreg) {
+    unsigned long long tot = 0;
+    for (int w = 0; w < NW; ++w) tot += red[threadIdx.x * NW + w];
+    if (tot && (threadIdx.x == 0 || threadIdx.x - 1 < q)) atomicAdd(slot + threadIdx.x, tot);
+  }
+  if (qreg == 0) {
+    for (int k = threadIdx.x; k < q; k += NTHREADS)
+      if (hist[k]) atomicAdd(slot + 1 + k, (unsigned long long)hist[k]);
+  }
+}
+
+constexpr int QREG = QREG_MAX;   // state counts kept in registers for q <= QREG
+
+}  // namespace fused
+using namespace fused;
+
+struct LabelTileSmem {
+  TileSmem tile;
+  uint32_t e_last;                                  // raw east bit of column w-1, bit = row
+  unsigned long long red[(1 + QREG) * (LABEL_THREADS / 32)];
+  int hist[128];
+};
+
+struct FlipTileSmem {
+  uint16_t rlist[TILE_SITES];
+  uint8_t ns[TILE_SITES];
+  uint32_t edge_mark[TILE_SITES / 32];
+  int warp_cnt[LABEL_THREADS / 32];
+};
+
+// One tile of the fused draw-and-label step (see k_fused.cu).  All threads
+// of the CTA call it; it synchronises the CTA internally and on return.
+__device__ __forceinline__ void sw_label_tile(const SwRep& R, int t, uint64_t sweep, bool do_obs, int obs_cap,
+                                              LabelTileSmem& ls) {
+  TileSmem& sm = ls.tile;
+  uint32_t& e_last = ls.e_last;
+  unsigned long long* red = ls.red;
+  int* hist = ls.hist;
+  const int8_t* __restrict__ spins = R.spins;
+  uint16_t* __restrict__ lroot = R.lroot;
+  int32_t* __restrict__ gpar = R.gpar;
+  const Grid& g = R.g;
+  const LabelScratch& s = R.s;
+  const int q = R.q;
+  const uint64_t T = R.T, seed = R.seed;
+  const int L = g.W;
+  const int ty = t / g.tiles_x, tx = t - ty * g.tiles_x;
+  const int y0 = ty * TILE_H, x0 = tx * TILE_W;
+  const int h = min(TILE_H, L - y0), w = min(TILE_W, L - x0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t* slot = s.roots + (int64_t)t * TILE_SITES;
+  int32_t* hook_log = s.work + (int64_t)t * TILE_SITES;
+  if (threadIdx.x == 0) {
+    sm.n_hooked = 0;
+    e_last = 0u;
+  }
+  for (int k = threadIdx.x; k < 128; k += LABEL_THREADS) hist[k] = 0;
+  __syncthreads();
+
+  // 1. bonds: warp c draws strip c, lane ly row ly
+  long long n_eq = 0;
+  int cnt[QREG];
+#pragma unroll
+  for (int k = 0; k < QREG; ++k) cnt[k] = 0;
+  {
+    const int ly = lane, c = warp;
+    const int nvalid = min(max(w - 32 * c, 0), 32);
+    unsigned long long wd = 0ull;
+    if (ly < h && nvalid > 0) {
+      const int y = y0 + ly, x = x0 + 32 * c;
+      const RowBonds rb = row_bonds(spins, L, y, x, nvalid, T, (uint32_t)seed, (uint32_t)(seed >> 32),
+                                    (uint32_t)sweep, (uint32_t)(sweep >> 32));
+      wd = rb.word;
+      if (32 * c + nvalid == w) {                 // east bond leaving the tile
+        const int bit = 2 * (nvalid - 1);
+        if ((wd >> bit) & 1ull) atomicOr(&e_last, 1u << ly);
+        wd &= ~(1ull << bit);
+      }
+      if (do_obs) {
+        const uint32_t valid = nvalid == 32 ? 0xFFFFFFFFu : ((1u << nvalid) - 1u);
+        n_eq = __popc(rb.eq_e & valid) + __popc(rb.eq_n & valid);
+        const int8_t* p = spins + (int64_t)y * L + x;
+        if (q <= QREG) {
+#pragma unroll
+          for (int k = 0; k < QREG; ++k)
+            if (k < q) cnt[k] = count_state(p, nvalid, k);
+        } else {
+          for (int j = 0; j < nvalid; ++j) atomicAdd(&hist[p[j]], 1);
+        }
+      }
+    }
+    sm.mb[ly * STRIPS + c] = wd;
+  }
+  __syncthreads();
+
+  // 2. label the tile
+  tile_engine(sm, h, w, slot, hook_log, s.err);
+
+  // 3. tile roots as 16-bit local indices, two sites per store
+  for (int k = threadIdx.x; k < TILE_SITES / 2; k += LABEL_THREADS) {
+    const int sidx = 2 * k;
+    const int ly = sidx >> TILE_W_LOG2, lx = sidx & (TILE_W - 1);
+    if (ly < h && lx < w) {   // w is a multiple of 4: both sites are inside
+      const uint32_t r0 = (uint32_t)sm.par[sm.par[sidx]], r1 = (uint32_t)sm.par[sm.par[sidx + 1]];
+      *reinterpret_cast<uint32_t*>(lroot + (int64_t)(y0 + ly) * L + x0 + lx) = r0 | (r1 << 16);
+    }
+  }
+
+  // 4. seam record; parent entries of edge roots
+  int32_t* rec = s.seams + (int64_t)t * SeamLayout::INTS;
+  auto groot = [&](int ly, int lx) -> int32_t { return tile_global(sm.par[sm.par[ly * TILE_W + lx]], y0, x0, L); };
+  auto init_parent = [&](bool ok, int32_t r) {
+    // one write per run of equal roots among consecutive lanes
+    const int32_t left = __shfl_up_sync(FULL, r, 1);
+    if (ok && (lane == 0 || left != r)) gpar[r] = r;
+  };
+  for (int k = threadIdx.x; k < TILE_H; k += LABEL_THREADS) {
+    const bool ok = k < h;
+    const int32_t a = ok ? groot(k, 0) : -1, b = ok ? groot(k, w - 1) : -1;
+    rec[SeamLayout::COL_L + k] = a;
+    rec[SeamLayout::COL_R + k] = b;
+    init_parent(ok, a);
+    init_parent(ok, b);
+    if (lane == 0) rec[SeamLayout::E_BITS + (k >> 5)] = (int32_t)e_last;
+  }
+  for (int k = threadIdx.x; k < TILE_W; k += LABEL_THREADS) {
+    const bool ok = k < w;
+    const int32_t a = ok ? groot(0, k) : -1, b = ok ? groot(h - 1, k) : -1;
+    rec[SeamLayout::ROW_B + k] = a;
+    rec[SeamLayout::ROW_T + k] = b;
+    init_parent(ok, a);
+    init_parent(ok, b);
+    const bool n = ok && ((sm.mb[(h - 1) * STRIPS + (k >> 5)] >> (2 * (k & 31) + 1)) & 1ull);
+    const uint32_t nb = __ballot_sync(FULL, n);
+    if (lane == 0) rec[SeamLayout::N_BITS + (k >> 5)] = (int32_t)nb;
+  }
+
+  // 5. observables of the spins read (the previous sweep's result)
+  if (do_obs) {
+    unsigned long long* oslot =
+        reinterpret_cast<unsigned long long*>(R.obs + (int64_t)((sweep - 1) % (uint64_t)obs_cap) * (q + 1));
+    add_observables<LABEL_THREADS>(n_eq, cnt, q, q <= QREG ? q : 0, oslot, red, hist);
+  }
+  __syncthreads();
+}
+
+// One tile of the fused flip step (see k_fused.cu).  All threads of the CTA
+// call it; it synchronises the CTA internally and on return.
+__device__ __forceinline__ void sw_flip_tile(const SwRep& R, int t, uint64_t sweep, int limit, FlipTileSmem& fs) {
+  // Thread t owns, in each of four passes j, the eight sites
+  // (row 8j + t/32, columns 8(t%32) .. 8(t%32)+7) of the tile: one 16-byte
+  // load of tile roots and one 8-byte store of spins per pass.
+  constexpr int PASSES = TILE_SITES / (8 * LABEL_THREADS);
+  static_assert(PASSES * 8 * LABEL_THREADS == TILE_SITES && TILE_W == 256, "site ownership");
+  uint16_t* rlist = fs.rlist;
+  uint8_t* ns = fs.ns;
+  uint32_t* edge_mark = fs.edge_mark;
+  int* warp_cnt = fs.warp_cnt;
+  int8_t* __restrict__ spins = R.spins;
+  const uint16_t* __restrict__ lroot = R.lroot;
+  int32_t* __restrict__ gpar = R.gpar;
+  const Grid& g = R.g;
+  const int q = R.q;
+  const uint64_t seed = R.seed;
+  int* err = R.s.err;
+  const int L = g.W;
+  const int ty = t / g.tiles_x, tx = t - ty * g.tiles_x;
+  const int y0 = ty * TILE_H, x0 = tx * TILE_W;
+  const int h = min(TILE_H, L - y0), w = min(TILE_W, L - x0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lx0 = 8 * lane;
+
+  // 1. tile roots of my sites (w is a multiple of 4: a group of eight sites is
+  //    either wholly inside, or its first four are)
+  uint4 r4[PASSES];
+#pragma unroll
+  for (int j = 0; j < PASSES; ++j) {
+    const int ly = 8 * j + warp;
+    const uint16_t* src = lroot + (int64_t)(y0 + ly) * L + x0 + lx0;
+    r4[j] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+    // 16-byte loads need L % 8 == 0; L % 4 == 0 always allows 8-byte loads
+    if (ly < h && lx0 + 8 <= w) {
+      if ((L & 7) == 0) {
+        r4[j] = *reinterpret_cast<const uint4*>(src);
+      } else {
+        const uint2 a = *reinterpret_cast<const uint2*>(src), b = *reinterpret_cast<const uint2*>(src + 4);
+        r4[j] = make_uint4(a.x, a.y, b.x, b.y);
+      }
+    } else if (ly < h && lx0 + 4 <= w) {
+      const uint2 v = *reinterpret_cast<const uint2*>(src);
+      r4[j].x = v.x;
+      r4[j].y = v.y;
+    }
+  }
+  for (int k = threadIdx.x; k < TILE_SITES / 32; k += LABEL_THREADS) edge_mark[k] = 0u;
+  __syncthreads();
+
+  auto root_of = [&](int j, int i) -> int {   // site i (0..7) of pass j
+    const uint32_t wv = (i < 2) ? r4[j].x : (i < 4) ? r4[j].y : (i < 6) ? r4[j].z : r4[j].w;
+    return (int)((wv >> (16 * (i & 1))) & 0xFFFFu);
+  };
+
+  // 2. roots on the tile edge (their clusters may continue outside the tile);
+  //    3. my roots
+  uint32_t mine = 0;   // bit 8j + i: site i of pass j is a root
+#pragma unroll
+  for (int j = 0; j < PASSES; ++j) {
+    const int ly = 8 * j + warp;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int lx = lx0 + i;
+      if (ly >= h || lx >= w) continue;
+      const int r = root_of(j, i);
+      if (ly == 0 || ly == h - 1 || lx == 0 || lx == w - 1) atomicOr(&edge_mark[r >> 5], 1u << (r & 31));
+      if (r == ly * TILE_W + lx) mine |= 1u << (8 * j + i);
+    }
+  }
+  const int cnt = __popc(mine);
+  int incl = cnt;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int v = __shfl_up_sync(FULL, incl, d);
+    if (lane >= d) incl += v;
+  }
+  if (lane == 31) warp_cnt[warp] = incl;
+  __syncthreads();
+  int base = 0, n_roots = 0;
+#pragma unroll
+  for (int k = 0; k < LABEL_THREADS / 32; ++k) {
+    base += (k < warp) ? warp_cnt[k] : 0;
+    n_roots += warp_cnt[k];
+  }
+  base += incl - cnt;
+  while (mine) {
+    const int b = __ffs(mine) - 1;
+    mine &= mine - 1;
+    rlist[base++] = (uint16_t)((8 * (b >> 3) + warp) * TILE_W + lx0 + (b & 7));
+  }
+  __syncthreads();
+
+  // 4. one draw per tile root, keyed by its cluster's final root
+  const uint32_t klo = (uint32_t)seed, khi = (uint32_t)(seed >> 32);
+  for (int k = threadIdx.x; k < n_roots; k += LABEL_THREADS) {
+    const int r = rlist[k];
+    int R = tile_global(r, y0, x0, L);
+    if ((edge_mark[r >> 5] >> (r & 31)) & 1u) R = g_find(gpar, R, limit, err);
+    const uint4 d = philox(make_uint4((uint32_t)R, (uint32_t)sweep, (uint32_t)(sweep >> 32), TAG_FLIP), klo, khi);
+    ns[r] = (uint8_t)state_of(d.x, q);
+  }
+  __syncthreads();
+
+  // 5. every site takes its tile root's state
+#pragma unroll
+  for (int j = 0; j < PASSES; ++j) {
+    const int ly = 8 * j + warp;
+    if (ly >= h || lx0 + 4 > w) continue;
+    uint32_t lo = 0, hi = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) lo |= (uint32_t)ns[root_of(j, i)] << (8 * i);
+    int8_t* dst = spins + (int64_t)(y0 + ly) * L + x0 + lx0;
+    *reinterpret_cast<uint32_t*>(dst) = lo;   // 4-byte aligned: L % 4 == 0
+    if (lx0 + 8 <= w) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) hi |= (uint32_t)ns[root_of(j, 4 + i)] << (8 * i);
+      *reinterpret_cast<uint32_t*>(dst + 4) = hi;
+    }
+  }
+  __syncthreads();
+}
+
+}  // namespace swccl

@@ -171,3 +171,31 @@ cudaError_t launch_check_spins(const int8_t* spins, int64_t n, int q, int* err, 
 }
 
 }  // namespace swccl
+
+namespace swccl {
+
+// ---------------------------------------------------------------------------
+// Measurement helper: Philox4x32-10 throughput with no memory traffic.  Each
+// thread makes `calls` independent calls (counter = thread id, call index)
+// and folds the outputs into one word, stored once so that nothing is
+// optimised away.  Times of this kernel give the integer-ALU ceiling of the
+// bond draws.
+__global__ void __launch_bounds__(256) k_philox_probe(long long calls, uint32_t* __restrict__ sink) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t acc = 0;
+  for (long long i = 0; i < calls; i += 4) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const uint4 r = philox(make_uint4(tid, (uint32_t)(i + u), 0u, TAG_BOND), 0x1234u, 0x5678u);
+      acc ^= r.x ^ r.y ^ r.z ^ r.w;
+    }
+  }
+  sink[tid] = acc;
+}
+
+cudaError_t launch_philox_probe(long long calls_per_thread, int blocks, uint32_t* sink, cudaStream_t st) {
+  k_philox_probe<<<blocks, 256, 0, st>>>(calls_per_thread, sink);
+  return cudaGetLastError();
+}
+
+}  // namespace swccl

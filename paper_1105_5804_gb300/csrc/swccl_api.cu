@@ -519,6 +519,13 @@ int ccl_perc_mask(uint64_t k, uint8_t* mask, int H, int W, void* stream) {
   return SW_OK;
 }
 
+int sw_probe_philox(int64_t calls_per_thread, int blocks, uint32_t* sink, void* stream) {
+  if (calls_per_thread < 4 || calls_per_thread % 4 != 0 || blocks < 1 || !sink)
+    return fail(SW_ERR_ARG, "sw_probe_philox: calls_per_thread must be a positive multiple of 4, blocks >= 1");
+  CK(launch_philox_probe(calls_per_thread, blocks, sink, static_cast<cudaStream_t>(stream)));
+  return SW_OK;
+}
+
 int ccl_status(void) {
   CK(cudaDeviceSynchronize());
   int* p = ccl_status_ptr();

@@ -84,6 +84,7 @@ cudaError_t launch_activate(const int8_t* spins, uint8_t* mask, int L, uint64_t 
 cudaError_t launch_perc_mask(uint8_t* mask, int H, int W, uint64_t k, cudaStream_t st);
 cudaError_t launch_pixel_bonds(const uint8_t* px, uint8_t* mask, int H, int W, int periodic,
                                cudaStream_t st);
+cudaError_t launch_philox_probe(long long calls_per_thread, int blocks, uint32_t* sink, cudaStream_t st);
 cudaError_t launch_check_spins(const int8_t* spins, int64_t n, int q, int* err, cudaStream_t st);
 
 cudaError_t launch_tile_label(const uint8_t* mask, int32_t* labels, const Grid& g,

@@ -88,3 +88,18 @@ def test_flip_uniform_per_cluster_and_constant_on_clusters(q):
     stat = ((counts - tot / q) ** 2 / (tot / q)).sum()
     assert chi2.sf(stat, q - 1) > 1e-4
     assert abs(np.mean(corr)) < 5 / math.sqrt(6 * roots.size)
+
+
+@pytest.mark.parametrize("q", [2, 3, 7])
+def test_hot_start_uniform_and_uncorrelated(q):
+    """Hot start (INIT draw per site): every state equally likely, no
+    correlation between neighbouring sites, different seeds differ."""
+    L = 256
+    s = oracle.init_spins(L, q, 123, True).astype(np.int64)
+    counts = np.bincount(s, minlength=q)
+    stat = ((counts - s.size / q) ** 2 / (s.size / q)).sum()
+    assert chi2.sf(stat, q - 1) > 1e-4
+    r = np.corrcoef(s[:-1], s[1:])[0, 1]
+    assert abs(r) < 5 / math.sqrt(s.size)
+    assert not np.array_equal(s, oracle.init_spins(L, q, 124, True))
+    assert not np.any(oracle.init_spins(L, q, 123, False))
