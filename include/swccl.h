@@ -182,6 +182,64 @@ int sw_set_timing(sw_handle* h, int enable);
 int sw_phase_times(sw_handle* h, double* ms, int64_t* n_sweeps);
 
 /* ------------------------------------------------------------------------ */
+/* Batches of independent chains (no counterpart in the paper: many         */
+/* replicas of uneven size and temperature advanced together)               */
+/* ------------------------------------------------------------------------ */
+
+/* How a batch runs one sweep of all its chains (the fused sweep of every
+ * chain: draw + label, merge, flip):
+ *   SW_BATCH_PHASES: one launch per step over the tiles of all chains;
+ *   SW_BATCH_PERSISTENT: one cooperative launch per sweep; its CTAs walk the
+ *     tiles of all chains step by step with grid barriers in between.  A
+ *     barrier wait is bounded (about 2 s): on expiry the kernel records
+ *     SW_ERR_TIMEOUT, returns, and later calls report it.
+ * One sweep of either schedule is captured as a CUDA graph and replayed
+ * (direct launches if capture is refused).  Both give, for every chain, the
+ * same result bit for bit as a single handle with the same arguments. */
+#define SW_BATCH_PHASES 0
+#define SW_BATCH_PERSISTENT 1
+
+typedef struct sw_batch sw_batch;
+
+/* n chains; chain r: L[r] x L[r] periodic lattice (4 <= L <= 46340,
+ * L % 4 == 0), q[r] states, inverse temperature beta[r], seed[r]; J = 1 and
+ * the coupling convention are shared; hot_start as in sw_create_ex.  The
+ * arrays are host memory, read during the call.  The batch owns all device
+ * memory (about 15.8 bytes per site plus a 4096-sweep observable ring per
+ * chain) and orders its work on `stream` (NULL: its own stream).  Default
+ * schedule SW_BATCH_PHASES.  NULL on failure (sw_last_error()). */
+sw_batch* sw_batch_create(int n, const int* L, const int* q, const double* beta, const uint64_t* seed,
+                          int convention, int hot_start, void* stream);
+
+/* Free the batch (waits for its stream).  NULL is accepted. */
+int sw_batch_destroy(sw_batch* b);
+
+/* Select the schedule for the following sweeps; blocks_per_sm caps the
+ * persistent kernel's CTAs per SM (0: as many as fit). */
+int sw_batch_set_schedule(sw_batch* b, int schedule, int blocks_per_sm);
+
+/* Enqueue n sweeps of every chain; returns without waiting. */
+int sw_batch_sweep(sw_batch* b, int n);
+
+/* Wait; report SW_ERR_TIMEOUT / SW_ERR_STATE recorded by the device. */
+int sw_batch_sync(sw_batch* b);
+
+/* Observables of chain `replica` as sw_observables (own read position per
+ * chain).  Synchronises. */
+int sw_batch_observables(sw_batch* b, int replica, int64_t* out, int max_sweeps, int* n_written);
+
+/* Spins of chain `replica` (int8[L*L]) to host or device memory.  Synchronises. */
+int sw_batch_get_spins(sw_batch* b, int replica, int8_t* dst, int is_device);
+
+/* info[0..7] = chains, total sites, total tiles, sweeps enqueued, schedule,
+ * persistent CTAs, 1 if the current schedule runs from a captured graph,
+ * observable ring capacity. */
+int sw_batch_info(sw_batch* b, int64_t* info);
+
+/* The CUDA stream of the batch. */
+void* sw_batch_stream(sw_batch* b);
+
+/* ------------------------------------------------------------------------ */
 /* Connected-component labeling of a bond mask (Sec. II.B, II.C)             */
 /* ------------------------------------------------------------------------ */
 

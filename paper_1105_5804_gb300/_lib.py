@@ -17,6 +17,7 @@ SW_OK, SW_ERR_ARG, SW_ERR_OOM, SW_ERR_CUDA, SW_ERR_TIMEOUT, SW_ERR_STATE = 0, 1,
 SW_CONV_AUTO, SW_CONV_POTTS, SW_CONV_ISING = 0, 1, 2
 SW_N_PHASES = 5
 SW_MODE_STAGED, SW_MODE_FUSED = 0, 1
+SW_BATCH_PHASES, SW_BATCH_PERSISTENT = 0, 1
 PHASE_NAMES = ("activate", "local", "merge", "roots", "flip")
 
 
@@ -65,6 +66,15 @@ def lib():
         "ccl_label_noalloc": ([vp, vp, i32, i32, i32, vp], i32),
         "ccl_status": ([], i32),
         "sw_probe_philox": ([i64, i32, vp, vp], i32),
+        "sw_batch_create": ([i32, vp, vp, vp, vp, i32, i32, vp], vp),
+        "sw_batch_destroy": ([vp], i32),
+        "sw_batch_set_schedule": ([vp, i32, i32], i32),
+        "sw_batch_sweep": ([vp, i32], i32),
+        "sw_batch_sync": ([vp], i32),
+        "sw_batch_observables": ([vp, i32, vp, i32, ctypes.POINTER(i32)], i32),
+        "sw_batch_get_spins": ([vp, i32, vp, i32], i32),
+        "sw_batch_info": ([vp, vp], i32),
+        "sw_batch_stream": ([vp], vp),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -290,3 +300,64 @@ def sw_probe_philox(calls_per_thread, blocks, sink, stream=None):
 
 def ccl_status():
     _check(lib().ccl_status())
+
+
+# ---------------------------------------------------------------------------
+# Batches of chains
+# ---------------------------------------------------------------------------
+def sw_batch_create(L, q, beta, seed, convention=SW_CONV_AUTO, hot_start=False, stream=0):
+    """L, q, beta, seed: sequences of equal length (one entry per chain)."""
+    n = len(L)
+    La = np.ascontiguousarray(L, dtype=np.int32)
+    qa = np.ascontiguousarray(q, dtype=np.int32)
+    ba = np.ascontiguousarray(beta, dtype=np.float64)
+    sa = np.ascontiguousarray(seed, dtype=np.uint64)
+    if not (qa.size == ba.size == sa.size == n):
+        raise ValueError("L, q, beta, seed must have equal lengths")
+    h = lib().sw_batch_create(n, La.ctypes.data, qa.ctypes.data, ba.ctypes.data, sa.ctypes.data, convention,
+                              1 if hot_start else 0, _stream(stream) if stream else None)
+    return _handle(h)
+
+
+def sw_batch_destroy(b):
+    _check(lib().sw_batch_destroy(b))
+
+
+def sw_batch_set_schedule(b, schedule, blocks_per_sm=0):
+    _check(lib().sw_batch_set_schedule(b, schedule, blocks_per_sm))
+
+
+def sw_batch_sweep(b, n):
+    _check(lib().sw_batch_sweep(b, n))
+
+
+def sw_batch_sync(b):
+    _check(lib().sw_batch_sync(b))
+
+
+def sw_batch_info(b):
+    info = np.zeros(8, dtype=np.int64)
+    _check(lib().sw_batch_info(b, info.ctypes.data))
+    keys = ("chains", "sites", "tiles", "sweeps", "schedule", "persistent_blocks", "graph", "obs_capacity")
+    return {k: int(v) for k, v in zip(keys, info)}
+
+
+def sw_batch_observables(b, replica, q, max_sweeps=4096):
+    out = np.zeros((max_sweeps, 1 + q), dtype=np.int64)
+    n = ctypes.c_int(0)
+    _check(lib().sw_batch_observables(b, replica, out.ctypes.data, max_sweeps, ctypes.byref(n)))
+    return out[: n.value]
+
+
+def sw_batch_get_spins(b, replica, L, out=None):
+    if out is None or isinstance(out, np.ndarray):
+        a = np.empty(L * L, dtype=np.int8) if out is None else out
+        _check(lib().sw_batch_get_spins(b, replica, a.ctypes.data, 0))
+        return a
+    import torch
+    _check(lib().sw_batch_get_spins(b, replica, _dev(out, torch.int8, L * L, "out"), 1))
+    return out
+
+
+def sw_batch_stream(b):
+    return int(lib().sw_batch_stream(b) or 0)

@@ -7,19 +7,6 @@
 
 namespace swccl {
 
-// One lattice as the fused kernels see it.
-struct SwRep {
-  int8_t* spins;      // L*L int8
-  uint16_t* lroot;    // L*L tile roots (local index)
-  int32_t* gpar;      // L*L parent entries (only edge roots are used)
-  int64_t* obs;       // observable ring: obs_cap x (1 + q)
-  LabelScratch s;     // per-tile pair lists, hook logs, seam records, status word
-  Grid g;             // L x L, periodic
-  uint64_t T, seed;
-  int q;
-  int tile0;          // first global tile of this lattice in a batch
-};
-
 namespace fused {
 
 // Four byte lanes of a and b compared: bit k of the result is set iff byte k
@@ -292,7 +279,8 @@ __device__ __forceinline__ void sw_flip_tile(const SwRep& R, int t, uint64_t swe
   const int lx0 = 8 * lane;
 
   // 1. tile roots of my sites (w is a multiple of 4: a group of eight sites is
-  //    either wholly inside, or its first four are)
+  //    either wholly inside, or its first four are); read through L2 because a
+  //    persistent kernel wrote them on other SMs
   uint4 r4[PASSES];
 #pragma unroll
   for (int j = 0; j < PASSES; ++j) {
@@ -302,13 +290,13 @@ __device__ __forceinline__ void sw_flip_tile(const SwRep& R, int t, uint64_t swe
     // 16-byte loads need L % 8 == 0; L % 4 == 0 always allows 8-byte loads
     if (ly < h && lx0 + 8 <= w) {
       if ((L & 7) == 0) {
-        r4[j] = *reinterpret_cast<const uint4*>(src);
+        r4[j] = __ldcg(reinterpret_cast<const uint4*>(src));
       } else {
-        const uint2 a = *reinterpret_cast<const uint2*>(src), b = *reinterpret_cast<const uint2*>(src + 4);
+        const uint2 a = __ldcg(reinterpret_cast<const uint2*>(src)), b = __ldcg(reinterpret_cast<const uint2*>(src + 4));
         r4[j] = make_uint4(a.x, a.y, b.x, b.y);
       }
     } else if (ly < h && lx0 + 4 <= w) {
-      const uint2 v = *reinterpret_cast<const uint2*>(src);
+      const uint2 v = __ldcg(reinterpret_cast<const uint2*>(src));
       r4[j].x = v.x;
       r4[j].y = v.y;
     }
@@ -386,6 +374,52 @@ __device__ __forceinline__ void sw_flip_tile(const SwRep& R, int t, uint64_t swe
       *reinterpret_cast<uint32_t*>(dst + 4) = hi;
     }
   }
+  __syncthreads();
+}
+
+// Observables of the current spins of tile t (bonds joining equal spins, the
+// tile's east and north bonds, and sites per state), added to the slot of
+// sweep `done`.  All threads of the CTA call it.
+__device__ __forceinline__ void observe_tile(const SwRep& R, int t, uint64_t done, int obs_cap, LabelTileSmem& ls) {
+  const Grid& g = R.g;
+  const int L = g.W, q = R.q;
+  const int ty = t / g.tiles_x, tx = t - ty * g.tiles_x;
+  const int y0 = ty * TILE_H, x0 = tx * TILE_W;
+  const int h = min(TILE_H, L - y0), w = min(TILE_W, L - x0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = threadIdx.x; k < 128; k += LABEL_THREADS) ls.hist[k] = 0;
+  __syncthreads();
+  long long n_eq = 0;
+  int cnt[QREG];
+#pragma unroll
+  for (int k = 0; k < QREG; ++k) cnt[k] = 0;
+  const int ly = lane, c = warp;
+  const int nvalid = min(max(w - 32 * c, 0), 32);
+  if (ly < h && nvalid > 0) {
+    const int y = y0 + ly, x = x0 + 32 * c;
+    const int yn = (y + 1 == L) ? 0 : y + 1;
+    const int8_t* row = R.spins + (int64_t)y * L;
+    const int8_t* rown = R.spins + (int64_t)yn * L;
+    const int nw = nvalid >> 2;
+    const int xe = (x + nvalid == L) ? 0 : x + nvalid;
+    const uint32_t east_byte = (uint32_t)(uint8_t)row[xe];
+    for (int k = 0; k < nw; ++k) {
+      const uint32_t cur = *reinterpret_cast<const uint32_t*>(row + x + 4 * k);
+      const uint32_t nor = *reinterpret_cast<const uint32_t*>(rown + x + 4 * k);
+      const uint32_t next = (k + 1 < nw) ? *reinterpret_cast<const uint32_t*>(row + x + 4 * k + 4) : east_byte;
+      n_eq += __popc(eq4(cur, (cur >> 8) | (next << 24))) + __popc(eq4(cur, nor));
+      if (q <= QREG) {
+#pragma unroll
+        for (int s = 0; s < QREG; ++s)
+          if (s < q) cnt[s] += __popc(eq4(cur, 0x01010101u * (uint32_t)s));
+      } else {
+        for (int j = 0; j < 4; ++j) atomicAdd(&ls.hist[(cur >> (8 * j)) & 0xFF], 1);
+      }
+    }
+  }
+  unsigned long long* oslot =
+      reinterpret_cast<unsigned long long*>(R.obs + (int64_t)(done % (uint64_t)obs_cap) * (q + 1));
+  add_observables<LABEL_THREADS>(n_eq, cnt, q, q <= QREG ? q : 0, oslot, ls.red, ls.hist);
   __syncthreads();
 }
 

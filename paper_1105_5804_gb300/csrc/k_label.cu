@@ -153,7 +153,6 @@ cudaError_t launch_tile_label(const uint8_t* mask, int32_t* labels, const Grid& 
 // Seam merge: thread k of tile t handles east seam bond k (k < TILE_H) or
 // north seam bond k - TILE_H.
 // ---------------------------------------------------------------------------
-constexpr int MERGE_PER_TILE = TILE_H + TILE_W;
 constexpr int MERGE_THREADS = 256;
 
 __global__ void __launch_bounds__(MERGE_THREADS)
@@ -161,41 +160,8 @@ k_merge(int32_t* __restrict__ labels, Grid g, LabelScratch s, int limit) {
   const int64_t gid = blockIdx.x * (int64_t)MERGE_THREADS + threadIdx.x;
   const int64_t total = (int64_t)g.n_tiles() * MERGE_PER_TILE;
   if (gid - (threadIdx.x & 31) >= total) return;   // whole warp past the end
-  int a = -1, b = -1;
-  bool valid = false;
-  if (gid < total) {
-    const int t = (int)(gid / MERGE_PER_TILE);
-    const int k = (int)(gid - (int64_t)t * MERGE_PER_TILE);
-    const int ty = t / g.tiles_x, tx = t - ty * g.tiles_x;
-    const int32_t* rec = s.seams + (int64_t)t * SeamLayout::INTS;
-    if (k < TILE_H) {
-      const bool has_east = g.periodic || tx + 1 < g.tiles_x;
-      const uint32_t ebits = (uint32_t)rec[SeamLayout::E_BITS + (k >> 5)];
-      if (has_east && ((ebits >> (k & 31)) & 1u)) {
-        const int te = ty * g.tiles_x + (tx + 1 == g.tiles_x ? 0 : tx + 1);
-        a = rec[SeamLayout::COL_R + k];
-        b = s.seams[(int64_t)te * SeamLayout::INTS + SeamLayout::COL_L + k];
-        valid = true;
-      }
-    } else {
-      const int lx = k - TILE_H;
-      const bool has_north = g.periodic || ty + 1 < g.tiles_y;
-      const uint32_t nbits = (uint32_t)rec[SeamLayout::N_BITS + (lx >> 5)];
-      if (has_north && ((nbits >> (lx & 31)) & 1u)) {
-        const int tn = (ty + 1 == g.tiles_y ? 0 : ty + 1) * g.tiles_x + tx;
-        a = rec[SeamLayout::ROW_T + lx];
-        b = s.seams[(int64_t)tn * SeamLayout::INTS + SeamLayout::ROW_B + lx];
-        valid = true;
-      }
-    }
-  }
-  valid = valid && a != b;
-  const unsigned long long key =
-      valid ? ((unsigned long long)(unsigned)min(a, b) << 32) | (unsigned)max(a, b) : ~0ull;
-  // consecutive seam bonds usually join the same two roots: one union per run
-  const unsigned long long prev = __shfl_up_sync(FULL, key, 1);
-  const bool leader = (threadIdx.x & 31) == 0 || prev != key;
-  if (valid && leader) g_union(labels, a, b, limit, s.err);
+  const int t = (int)(gid / MERGE_PER_TILE);
+  merge_seam_bond(labels, g, s, t, (int)(gid - (int64_t)t * MERGE_PER_TILE), gid < total, limit);
 }
 
 cudaError_t launch_merge(int32_t* labels, const Grid& g, const LabelScratch& s, cudaStream_t st) {

@@ -70,6 +70,40 @@ struct SwCtl {
   int pad;
 };
 
+// One lattice as the fused kernels see it (also one replica of a batch).
+struct SwRep {
+  int8_t* spins;      // L*L int8
+  uint16_t* lroot;    // L*L tile roots (local index)
+  int32_t* gpar;      // L*L parent entries (only edge roots are used)
+  int64_t* obs;       // observable ring: obs_cap x (1 + q)
+  LabelScratch s;     // per-tile pair lists, hook logs, seam records, status word
+  Grid g;             // L x L, periodic
+  uint64_t T, seed;
+  int q;
+  int tile0;          // first global tile of this lattice in a batch
+};
+
+// Control block of a batch of chains (all replicas advance together).
+struct BatchCtl {
+  unsigned long long sweep;
+  long long obs_done;
+  int err;
+  unsigned int bar_count;    // grid barrier of the persistent kernel
+  unsigned int bar_gen;
+  int pad;
+};
+
+// What the batched kernels read: replica table and tile -> replica map, in
+// device memory.
+struct BatchView {
+  const SwRep* reps;
+  const int* tile_rep;
+  int n_reps;
+  int n_tiles;
+  int obs_cap;
+  int limit;          // union-find step bound: largest replica's sites + 64
+};
+
 // Bytes of LabelScratch for a grid (each part 256-byte aligned).
 int64_t label_scratch_bytes(const Grid& g);
 LabelScratch carve_label_scratch(const Grid& g, void* base, int* err);
@@ -110,6 +144,17 @@ cudaError_t launch_sw_flip(int8_t* spins, const uint16_t* lroot, int32_t* gpar, 
 cudaError_t launch_observe(const int8_t* spins, int L, int q, SwCtl* ctl, int64_t* obs, int obs_cap,
                            cudaStream_t st);
 cudaError_t launch_advance_fused(SwCtl* ctl, int64_t* obs, int obs_cap, int q, cudaStream_t st);
+
+// Batched chains (k_batch.cu).
+cudaError_t launch_batch_label(const BatchView& b, BatchCtl* ctl, cudaStream_t st);
+cudaError_t launch_batch_merge(const BatchView& b, cudaStream_t st);
+cudaError_t launch_batch_flip(const BatchView& b, BatchCtl* ctl, cudaStream_t st);
+cudaError_t launch_batch_advance(const BatchView& b, BatchCtl* ctl, cudaStream_t st);
+cudaError_t launch_batch_observe(const BatchView& b, BatchCtl* ctl, cudaStream_t st);
+// One persistent cooperative launch for the whole sweep; `blocks` CTAs.
+cudaError_t launch_batch_persistent(const BatchView& b, BatchCtl* ctl, int blocks, cudaStream_t st);
+// Largest number of co-resident CTAs of the persistent kernel per SM.
+int batch_persistent_blocks_per_sm();
 
 // Host helpers of the C ABI: set this thread's sw_last_error() message and
 // return `code`; device address of the stand-alone labeling status word on

@@ -137,4 +137,53 @@ __device__ __forceinline__ void tile_engine(TileSmem& sm, int h, int w, int32_t*
   __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// Seam merge (Sec. II.C): bond k of tile t leaves the tile east (k < TILE_H,
+// row k) or north (k >= TILE_H, column k - TILE_H), the periodic wrap
+// included.  If it is open, the two tile roots on its ends are joined on the
+// global array `gpar` (atomicMin hooking, larger root under the smaller).  A
+// lane whose root pair equals its left neighbour's skips the union, so runs
+// of seam bonds of one cluster cost one union.  All 32 lanes of a warp must
+// call together (active == false for lanes past the end); MERGE_PER_TILE is
+// a multiple of 32, so a warp never spans two tiles.  Seam records are read
+// through L2 (ld.cg): in a persistent kernel they were written by other SMs.
+constexpr int MERGE_PER_TILE = TILE_H + TILE_W;
+static_assert(MERGE_PER_TILE % 32 == 0, "warps must not straddle tiles");
+
+__device__ __forceinline__ void merge_seam_bond(int32_t* gpar, const Grid& g, const LabelScratch& s, int t, int k,
+                                                bool active, int limit) {
+  int a = -1, b = -1;
+  bool valid = false;
+  if (active) {
+    const int ty = t / g.tiles_x, tx = t - ty * g.tiles_x;
+    const int32_t* rec = s.seams + (int64_t)t * SeamLayout::INTS;
+    if (k < TILE_H) {
+      const bool has_east = g.periodic || tx + 1 < g.tiles_x;
+      const uint32_t ebits = (uint32_t)__ldcg(rec + SeamLayout::E_BITS + (k >> 5));
+      if (has_east && ((ebits >> (k & 31)) & 1u)) {
+        const int te = ty * g.tiles_x + (tx + 1 == g.tiles_x ? 0 : tx + 1);
+        a = __ldcg(rec + SeamLayout::COL_R + k);
+        b = __ldcg(s.seams + (int64_t)te * SeamLayout::INTS + SeamLayout::COL_L + k);
+        valid = true;
+      }
+    } else {
+      const int lx = k - TILE_H;
+      const bool has_north = g.periodic || ty + 1 < g.tiles_y;
+      const uint32_t nbits = (uint32_t)__ldcg(rec + SeamLayout::N_BITS + (lx >> 5));
+      if (has_north && ((nbits >> (lx & 31)) & 1u)) {
+        const int tn = (ty + 1 == g.tiles_y ? 0 : ty + 1) * g.tiles_x + tx;
+        a = __ldcg(rec + SeamLayout::ROW_T + lx);
+        b = __ldcg(s.seams + (int64_t)tn * SeamLayout::INTS + SeamLayout::ROW_B + lx);
+        valid = true;
+      }
+    }
+  }
+  valid = valid && a != b;
+  const unsigned long long key =
+      valid ? ((unsigned long long)(unsigned)min(a, b) << 32) | (unsigned)max(a, b) : ~0ull;
+  const unsigned long long prev = __shfl_up_sync(FULL, key, 1);
+  const bool leader = (threadIdx.x & 31) == 0 || prev != key;
+  if (valid && leader) g_union(gpar, a, b, limit, s.err);
+}
+
 }  // namespace swccl
