@@ -250,6 +250,56 @@ def philox_ceiling(torch, sw, reps=3):
     return blocks * 256 * calls / (best * 1e-3)
 
 
+def batch_secondary(torch, sw, sweeps=50, single_sweeps=5):
+    """The batched workload: 512 independent Ising chains, L log-uniform in
+    [64, 2048] (multiples of 32), beta spread over [0.9, 1.1] beta_c, seed =
+    chain id, cold start.  Site-updates/ns of the autotuned batch, of each
+    schedule, and of the same chains launched one at a time on one stream."""
+    from paper_1105_5804_gb300 import autotune, inputs
+    reps = inputs.batched_replicas()
+    L = [r["L"] for r in reps]
+    beta = [r["beta"] for r in reps]
+    seed = [r["seed"] for r in reps]
+    q = [2] * len(L)
+    total = sum(l * l for l in L)
+    choice = autotune.tune(L, q, beta, sw.SW_CONV_ISING, use_cache=False)
+    b = sw.sw_batch_create(L, q, beta, seed, sw.SW_CONV_ISING, False)
+    res = {"workload": "sw_batch_512_ising_L64-2048_beta0.9-1.1betac", "chains": len(L), "sites": total,
+           "unit": "site-updates/ns", "sweeps": sweeps, "autotune": choice}
+    try:
+        for name, sched, bps in (("phases", sw.SW_BATCH_PHASES, 0), ("persistent", sw.SW_BATCH_PERSISTENT, 0),
+                                 ("autotuned", choice["schedule"], choice["blocks_per_sm"])):
+            sw.sw_batch_set_schedule(b, sched, bps)
+            sw.sw_batch_sweep(b, 3)
+            ms = autotune.time_batch(b, sweeps)
+            res[name] = total * sweeps / (ms * 1e6)
+        res["value"] = res["autotuned"]
+        res["graph"] = bool(sw.sw_batch_info(b)["graph"])
+    finally:
+        sw.sw_batch_destroy(b)
+    # the same chains, one handle each, launched one after another on one stream
+    st = torch.cuda.Stream()
+    hs = [sw.sw_create_ex(L[r], 2, beta[r], 1.0, sw.SW_CONV_ISING, seed[r], False, st) for r in range(len(L))]
+    try:
+        for h in hs:
+            sw.sw_sweep(h, 1)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(single_sweeps):
+            for h in hs:
+                sw.sw_sweep(h, 1)
+        e1.record(st)
+        torch.cuda.synchronize()
+        res["one_at_a_time"] = total * single_sweeps / (e0.elapsed_time(e1) * 1e6)
+    finally:
+        for h in hs:
+            sw.sw_destroy(h)
+    res["batched_over_one_at_a_time"] = res["value"] / res["one_at_a_time"]
+    return res
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -337,6 +387,7 @@ def run_ours(args):
         secondary["sw_potts_q4_L16384"] = {"value": N * 50 / (a.elapsed_time(b) * 1e6),
                                            "unit": "site-updates/ns", "beta": math.log(3.0), "sweeps": 50}
         sw.sw_destroy(h4)
+        secondary["batch_512"] = batch_secondary(torch, sw)
     sw.sw_destroy(h)
 
     if rank != 0:

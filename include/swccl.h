@@ -299,6 +299,23 @@ int ccl_perc_mask(uint64_t k, uint8_t* mask, int H, int W, void* stream);
  * anything is launched.  Device-side failures are reported by ccl_status(). */
 int ccl_label_noalloc(const uint8_t* bond_mask, int32_t* labels, int H, int W, int periodic, void* stream);
 
+/* Bytes of workspace ccl_label_batch needs for n grids of sizes H[j] x W[j]
+ * (host arrays); -1 if a size is invalid. */
+int64_t ccl_batch_workspace_bytes(int n, const int* H, const int* W);
+
+/* Label n grids in one set of launches (one launch per step over the tiles
+ * of all grids); grid j: mask masks[j] -> labels labels[j] (device
+ * pointers, layouts as ccl_label), H[j] x W[j], periodic[j].  The pointer
+ * and size arrays are host memory, read during the call.  `workspace` is a
+ * device pointer of at least ccl_batch_workspace_bytes(n, H, W) bytes,
+ * 256-byte aligned; calls sharing a workspace must be ordered.  Each grid's
+ * labels equal what ccl_label gives for it alone.  The paper labels one
+ * lattice at a time; this batched form serves many small jobs (image
+ * segmentation requests) with few launches.  Device-side failures are
+ * reported by ccl_status(). */
+int ccl_label_batch(int n, const uint8_t* const* masks, int32_t* const* labels, const int* H, const int* W,
+                    const int* periodic, void* workspace, int64_t ws_bytes, void* stream);
+
 /* Wait for the whole device and return the first device-side failure
  * recorded by ccl_* kernels since the last call (SW_OK if none); clears it. */
 int ccl_status(void);

@@ -17,6 +17,7 @@ from ._lib import (  # noqa: F401
     ccl_label_noalloc, CCL_NOALLOC_SCRATCH_BYTES, sw_probe_philox,
     SW_BATCH_PHASES, SW_BATCH_PERSISTENT, sw_batch_create, sw_batch_destroy, sw_batch_set_schedule,
     sw_batch_sweep, sw_batch_sync, sw_batch_info, sw_batch_observables, sw_batch_get_spins, sw_batch_stream,
+    ccl_batch_workspace_bytes, ccl_label_batch,
 )
 
 

@@ -66,6 +66,8 @@ def lib():
         "ccl_label_noalloc": ([vp, vp, i32, i32, i32, vp], i32),
         "ccl_status": ([], i32),
         "sw_probe_philox": ([i64, i32, vp, vp], i32),
+        "ccl_batch_workspace_bytes": ([i32, vp, vp], i64),
+        "ccl_label_batch": ([i32, vp, vp, vp, vp, vp, vp, i64, vp], i32),
         "sw_batch_create": ([i32, vp, vp, vp, vp, i32, i32, vp], vp),
         "sw_batch_destroy": ([vp], i32),
         "sw_batch_set_schedule": ([vp, i32, i32], i32),
@@ -361,3 +363,34 @@ def sw_batch_get_spins(b, replica, L, out=None):
 
 def sw_batch_stream(b):
     return int(lib().sw_batch_stream(b) or 0)
+
+
+# ---------------------------------------------------------------------------
+# Batched labeling
+# ---------------------------------------------------------------------------
+def ccl_batch_workspace_bytes(H, W):
+    Ha = np.ascontiguousarray(H, dtype=np.int32)
+    Wa = np.ascontiguousarray(W, dtype=np.int32)
+    return int(lib().ccl_batch_workspace_bytes(len(Ha), Ha.ctypes.data, Wa.ctypes.data))
+
+
+def ccl_label_batch(masks, labels, H, W, periodic, workspace, stream=None):
+    """masks / labels: sequences of CUDA tensors (uint8 packed masks, int32
+    labels); H, W, periodic: sequences of ints."""
+    import torch
+    n = len(masks)
+    Ha = np.ascontiguousarray(H, dtype=np.int32)
+    Wa = np.ascontiguousarray(W, dtype=np.int32)
+    Pa = np.ascontiguousarray([1 if p else 0 for p in periodic], dtype=np.int32)
+    if not (len(labels) == Ha.size == Wa.size == Pa.size == n):
+        raise ValueError("masks, labels, H, W, periodic must have equal lengths")
+    mp = (ctypes.c_void_p * max(n, 1))()
+    lp = (ctypes.c_void_p * max(n, 1))()
+    for j in range(n):
+        N = int(Ha[j]) * int(Wa[j])
+        mp[j] = _dev(masks[j], torch.uint8, mask_bytes(N), "masks[%d]" % j).value
+        lp[j] = _dev(labels[j], torch.int32, N, "labels[%d]" % j).value
+    _check(lib().ccl_label_batch(n, mp, lp, Ha.ctypes.data, Wa.ctypes.data, Pa.ctypes.data,
+                                 _dev(workspace, torch.uint8, None, "workspace"), workspace.numel(),
+                                 _stream(stream)))
+    return labels

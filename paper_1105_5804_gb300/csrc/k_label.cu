@@ -28,119 +28,15 @@
 //                 cluster's new state here (Sec. II.D), keyed by the root.
 //  k_site_compress  label[i] = label[label[i]] for every site (stand-alone
 //                 labeling only: leaves every label canonical).
-#include "tile_engine.cuh"
+#include "label_tile.cuh"
 
 namespace swccl {
 
 
-// Local labeling of one tile for the stand-alone labeling path: the tile's
-// bond bits are copied from the packed mask into shared memory (bits of
-// sites outside the grid and the east bond of the tile's last column
-// cleared), the engine of tile_engine.cuh labels the tile, and the kernel
-// writes every site's label (global index of its tile root, the minimum
-// site index of its tile component), the tile's root list, and the seam
-// record (labels and outgoing bond bits of the four tile edges).
 __global__ void __launch_bounds__(LABEL_THREADS)
-k_tile_label(const uint8_t* __restrict__ mask, int32_t* __restrict__ labels, Grid g,
-             LabelScratch s) {
+k_tile_label(const uint8_t* __restrict__ mask, int32_t* __restrict__ labels, Grid g, LabelScratch s) {
   __shared__ TileSmem sm;
-  int* par = sm.par;
-  unsigned long long* mb = sm.mb;
-  int* warp_roots = sm.warp_roots;
-
-  const int t = blockIdx.x;
-  const int ty = t / g.tiles_x, tx = t - ty * g.tiles_x;
-  const int y0 = ty * TILE_H, x0 = tx * TILE_W;
-  const int h = min(TILE_H, g.H - y0), w = min(TILE_W, g.W - x0);
-  const int W = g.W;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int32_t* slot = s.roots + (int64_t)t * TILE_SITES;     // pair lists, later the root list
-  int32_t* hook_log = s.work + (int64_t)t * TILE_SITES;
-  if (threadIdx.x == 0) sm.n_hooked = 0;
-
-  // 1. bond bits
-  for (int k = threadIdx.x; k < TILE_H * STRIPS; k += LABEL_THREADS) {
-    const int ly = k / STRIPS, c = k - ly * STRIPS;
-    const int nvalid = min(max(w - 32 * c, 0), 32);
-    unsigned long long wd = 0ull;
-    if (ly < h && nvalid > 0) {
-      const int64_t site0 = (int64_t)(y0 + ly) * W + x0 + 32 * c;
-      if ((W & 31) == 0 && (reinterpret_cast<uintptr_t>(mask) & 7) == 0) {
-        wd = reinterpret_cast<const unsigned long long*>(mask)[site0 >> 5];
-      } else {
-        for (int i = 0; i < nvalid; ++i) wd |= (unsigned long long)site_bits(mask, site0 + i) << (2 * i);
-      }
-      if (nvalid < 32) wd &= (1ull << (2 * nvalid)) - 1ull;
-      if (32 * c + nvalid == w) wd &= ~(1ull << (2 * (nvalid - 1)));   // east bond leaving the tile
-    }
-    mb[k] = wd;
-  }
-  __syncthreads();
-
-  // 2-4a. label the tile
-  tile_engine(sm, h, w, slot, hook_log, s.err);
-
-  // 4b. every site's root; global labels; root list
-  constexpr int PER_T = TILE_SITES / LABEL_THREADS;
-  uint32_t mine = 0;      // bit j: site threadIdx.x + j*LABEL_THREADS is a root
-#pragma unroll 4
-  for (int j = 0; j < PER_T; ++j) {
-    const int sidx = threadIdx.x + j * LABEL_THREADS;
-    const int ly = sidx >> TILE_W_LOG2, lx = sidx & (TILE_W - 1);
-    if (ly < h && lx < w) {
-      const int p = par[sidx];
-      const int r = par[p];
-      labels[(int64_t)(y0 + ly) * W + x0 + lx] = (y0 + (r >> TILE_W_LOG2)) * W + x0 + (r & (TILE_W - 1));
-      if (r == sidx) mine |= 1u << j;
-    }
-  }
-  int cnt = __popc(mine), incl = cnt;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const int v = __shfl_up_sync(FULL, incl, d);
-    if (lane >= d) incl += v;
-  }
-  if (lane == 31) warp_roots[warp] = incl;
-  __syncthreads();
-  int base = 0, total = 0;
-#pragma unroll
-  for (int k = 0; k < LABEL_THREADS / 32; ++k) {
-    const int c = warp_roots[k];
-    base += (k < warp) ? c : 0;
-    total += c;
-  }
-  base += incl - cnt;
-  while (mine) {
-    const int j = __ffs(mine) - 1;
-    mine &= mine - 1;
-    const int sidx = threadIdx.x + j * LABEL_THREADS;
-    slot[base++] =
-        (y0 + (sidx >> TILE_W_LOG2)) * W + x0 + (sidx & (TILE_W - 1));
-  }
-
-  // 5. seam record
-  int32_t* rec = s.seams + (int64_t)t * SeamLayout::INTS;
-  auto glabel = [&](int ly, int lx) -> int32_t {
-    const int r = par[par[ly * TILE_W + lx]];
-    return (y0 + (r >> TILE_W_LOG2)) * W + x0 + (r & (TILE_W - 1));
-  };
-  for (int k = threadIdx.x; k < TILE_H; k += LABEL_THREADS) {
-    const bool ok = k < h;
-    rec[SeamLayout::COL_L + k] = ok ? glabel(k, 0) : -1;
-    rec[SeamLayout::COL_R + k] = ok ? glabel(k, w - 1) : -1;
-    const bool e = ok && (site_bits(mask, (int64_t)(y0 + k) * W + x0 + w - 1) & 1u);
-    const uint32_t eb = __ballot_sync(FULL, e);
-    if (lane == 0) rec[SeamLayout::E_BITS + (k >> 5)] = (int32_t)eb;
-  }
-  for (int k = threadIdx.x; k < TILE_W; k += LABEL_THREADS) {
-    const bool ok = k < w;
-    rec[SeamLayout::ROW_B + k] = ok ? glabel(0, k) : -1;
-    rec[SeamLayout::ROW_T + k] = ok ? glabel(h - 1, k) : -1;
-    const bool n = ok && ((mb[(h - 1) * STRIPS + (k >> 5)] >> (2 * (k & 31) + 1)) & 1ull);
-    const uint32_t nb = __ballot_sync(FULL, n);
-    if (lane == 0) rec[SeamLayout::N_BITS + (k >> 5)] = (int32_t)nb;
-  }
-  if (threadIdx.x == 0) s.root_counts[t] = total;
+  ccl_label_tile(mask, labels, g, s, blockIdx.x, sm);
 }
 
 cudaError_t launch_tile_label(const uint8_t* mask, int32_t* labels, const Grid& g,
@@ -180,17 +76,7 @@ constexpr int ROOT_THREADS = 256;
 __global__ void __launch_bounds__(ROOT_THREADS)
 k_root_compress(int32_t* __restrict__ labels, Grid g, LabelScratch s, int8_t* __restrict__ spins,
                 int q, uint64_t seed, const SwCtl* __restrict__ ctl, int limit) {
-  const int t = blockIdx.x;
-  const int n = s.root_counts[t];
-  const int32_t* list = s.roots + (int64_t)t * TILE_SITES;
-  uint64_t sweep = 0;
-  if (spins) sweep = ctl->sweep;
-  for (int k = threadIdx.x; k < n; k += ROOT_THREADS) {
-    const int r = list[k];
-    const int R = g_find(labels, r, limit, s.err);
-    if (R != r) atomicMin(labels + r, R);
-    if (spins && R == r) spins[r] = (int8_t)state_of(draw((uint32_t)r, sweep, TAG_FLIP, seed).x, q);
-  }
+  root_compress_tile(labels, s, blockIdx.x, spins, q, seed, spins ? ctl->sweep : 0, limit);
 }
 
 cudaError_t launch_root_compress(int32_t* labels, const Grid& g, const LabelScratch& s,

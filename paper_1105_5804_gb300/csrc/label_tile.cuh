@@ -1,0 +1,152 @@
+// label_tile.cuh -- per-tile bodies of the stand-alone labeling path, shared
+// by the single-grid kernels (k_label.cu) and the batched kernels over many
+// grids (k_ccl_batch.cu): local labeling of a tile from the packed mask, root
+// compression of a tile's root list, and the site pass that makes a tile's
+// labels canonical.
+#pragma once
+#include "tile_engine.cuh"
+
+namespace swccl {
+
+// Local labeling of one tile for the stand-alone labeling path: the tile's
+// bond bits are copied from the packed mask into shared memory (bits of
+// sites outside the grid and the east bond of the tile's last column
+// cleared), the engine of tile_engine.cuh labels the tile, and the kernel
+// writes every site's label (global index of its tile root, the minimum
+// site index of its tile component), the tile's root list, and the seam
+// record (labels and outgoing bond bits of the four tile edges).
+__device__ __forceinline__ void ccl_label_tile(const uint8_t* __restrict__ mask, int32_t* __restrict__ labels,
+                                               const Grid& g, const LabelScratch& s, int t, TileSmem& sm) {
+  int* par = sm.par;
+  unsigned long long* mb = sm.mb;
+  int* warp_roots = sm.warp_roots;
+
+  const int ty = t / g.tiles_x, tx = t - ty * g.tiles_x;
+  const int y0 = ty * TILE_H, x0 = tx * TILE_W;
+  const int h = min(TILE_H, g.H - y0), w = min(TILE_W, g.W - x0);
+  const int W = g.W;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t* slot = s.roots + (int64_t)t * TILE_SITES;     // pair lists, later the root list
+  int32_t* hook_log = s.work + (int64_t)t * TILE_SITES;
+  if (threadIdx.x == 0) sm.n_hooked = 0;
+
+  // 1. bond bits
+  for (int k = threadIdx.x; k < TILE_H * STRIPS; k += LABEL_THREADS) {
+    const int ly = k / STRIPS, c = k - ly * STRIPS;
+    const int nvalid = min(max(w - 32 * c, 0), 32);
+    unsigned long long wd = 0ull;
+    if (ly < h && nvalid > 0) {
+      const int64_t site0 = (int64_t)(y0 + ly) * W + x0 + 32 * c;
+      if ((W & 31) == 0 && (reinterpret_cast<uintptr_t>(mask) & 7) == 0) {
+        wd = reinterpret_cast<const unsigned long long*>(mask)[site0 >> 5];
+      } else {
+        for (int i = 0; i < nvalid; ++i) wd |= (unsigned long long)site_bits(mask, site0 + i) << (2 * i);
+      }
+      if (nvalid < 32) wd &= (1ull << (2 * nvalid)) - 1ull;
+      if (32 * c + nvalid == w) wd &= ~(1ull << (2 * (nvalid - 1)));   // east bond leaving the tile
+    }
+    mb[k] = wd;
+  }
+  __syncthreads();
+
+  // 2-4a. label the tile
+  tile_engine(sm, h, w, slot, hook_log, s.err);
+
+  // 4b. every site's root; global labels; root list
+  constexpr int PER_T = TILE_SITES / LABEL_THREADS;
+  uint32_t mine = 0;      // bit j: site threadIdx.x + j*LABEL_THREADS is a root
+#pragma unroll 4
+  for (int j = 0; j < PER_T; ++j) {
+    const int sidx = threadIdx.x + j * LABEL_THREADS;
+    const int ly = sidx >> TILE_W_LOG2, lx = sidx & (TILE_W - 1);
+    if (ly < h && lx < w) {
+      const int p = par[sidx];
+      const int r = par[p];
+      labels[(int64_t)(y0 + ly) * W + x0 + lx] = (y0 + (r >> TILE_W_LOG2)) * W + x0 + (r & (TILE_W - 1));
+      if (r == sidx) mine |= 1u << j;
+    }
+  }
+  int cnt = __popc(mine), incl = cnt;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int v = __shfl_up_sync(FULL, incl, d);
+    if (lane >= d) incl += v;
+  }
+  if (lane == 31) warp_roots[warp] = incl;
+  __syncthreads();
+  int base = 0, total = 0;
+#pragma unroll
+  for (int k = 0; k < LABEL_THREADS / 32; ++k) {
+    const int c = warp_roots[k];
+    base += (k < warp) ? c : 0;
+    total += c;
+  }
+  base += incl - cnt;
+  while (mine) {
+    const int j = __ffs(mine) - 1;
+    mine &= mine - 1;
+    const int sidx = threadIdx.x + j * LABEL_THREADS;
+    slot[base++] =
+        (y0 + (sidx >> TILE_W_LOG2)) * W + x0 + (sidx & (TILE_W - 1));
+  }
+
+  // 5. seam record
+  int32_t* rec = s.seams + (int64_t)t * SeamLayout::INTS;
+  auto glabel = [&](int ly, int lx) -> int32_t {
+    const int r = par[par[ly * TILE_W + lx]];
+    return (y0 + (r >> TILE_W_LOG2)) * W + x0 + (r & (TILE_W - 1));
+  };
+  for (int k = threadIdx.x; k < TILE_H; k += LABEL_THREADS) {
+    const bool ok = k < h;
+    rec[SeamLayout::COL_L + k] = ok ? glabel(k, 0) : -1;
+    rec[SeamLayout::COL_R + k] = ok ? glabel(k, w - 1) : -1;
+    const bool e = ok && (site_bits(mask, (int64_t)(y0 + k) * W + x0 + w - 1) & 1u);
+    const uint32_t eb = __ballot_sync(FULL, e);
+    if (lane == 0) rec[SeamLayout::E_BITS + (k >> 5)] = (int32_t)eb;
+  }
+  for (int k = threadIdx.x; k < TILE_W; k += LABEL_THREADS) {
+    const bool ok = k < w;
+    rec[SeamLayout::ROW_B + k] = ok ? glabel(0, k) : -1;
+    rec[SeamLayout::ROW_T + k] = ok ? glabel(h - 1, k) : -1;
+    const bool n = ok && ((mb[(h - 1) * STRIPS + (k >> 5)] >> (2 * (k & 31) + 1)) & 1ull);
+    const uint32_t nb = __ballot_sync(FULL, n);
+    if (lane == 0) rec[SeamLayout::N_BITS + (k >> 5)] = (int32_t)nb;
+  }
+  if (threadIdx.x == 0) s.root_counts[t] = total;
+  __syncthreads();
+}
+
+// Tile t's roots: label = final root; in a Swendsen-Wang sweep (spins set)
+// final roots also draw their cluster's new state.  All threads call it.
+__device__ __forceinline__ void root_compress_tile(int32_t* __restrict__ labels, const LabelScratch& s, int t,
+                                                   int8_t* __restrict__ spins, int q, uint64_t seed, uint64_t sweep,
+                                                   int limit) {
+  const int n = __ldcg(s.root_counts + t);
+  const int32_t* list = s.roots + (int64_t)t * TILE_SITES;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const int r = __ldcg(list + k);
+    const int R = g_find(labels, r, limit, s.err);
+    if (R != r) atomicMin(labels + r, R);
+    if (spins && R == r) spins[r] = (int8_t)state_of(draw((uint32_t)r, sweep, TAG_FLIP, seed).x, q);
+  }
+}
+
+// Site pass of tile t: every label of the tile points at a tile root whose
+// entry holds the final root after root compression; one jump makes the
+// label canonical.
+__device__ __forceinline__ void site_compress_tile(int32_t* __restrict__ labels, const Grid& g, int t) {
+  const int ty = t / g.tiles_x, tx = t - ty * g.tiles_x;
+  const int y0 = ty * TILE_H, x0 = tx * TILE_W;
+  const int h = min(TILE_H, g.H - y0), w = min(TILE_W, g.W - x0);
+  for (int k = threadIdx.x; k < TILE_SITES; k += blockDim.x) {
+    const int ly = k >> TILE_W_LOG2, lx = k & (TILE_W - 1);
+    if (ly < h && lx < w) {
+      int32_t* p = labels + (int64_t)(y0 + ly) * g.W + x0 + lx;
+      const int r = __ldcg(p);
+      const int R = __ldcg(labels + r);
+      if (R != r) *p = R;
+    }
+  }
+}
+
+}  // namespace swccl

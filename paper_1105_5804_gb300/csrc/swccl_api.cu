@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -516,6 +517,82 @@ int ccl_perc_mask(uint64_t k, uint8_t* mask, int H, int W, void* stream) {
   int rc = ccl_validate(mask, mask, H, W);
   if (rc) return rc;
   CK(launch_perc_mask(mask, H, W, k, static_cast<cudaStream_t>(stream)));
+  return SW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched labeling
+// ---------------------------------------------------------------------------
+namespace {
+inline int64_t al256b(int64_t b) { return (b + 255) & ~(int64_t)255; }
+
+int64_t ccl_batch_bytes(int n, const int* H, const int* W, int64_t* n_tiles_out) {
+  int64_t tiles = 0, scratch = 0;
+  for (int j = 0; j < n; ++j) {
+    if (H[j] < 1 || W[j] < 1 || (int64_t)H[j] * W[j] >= ((int64_t)1 << 31)) return -1;
+    const Grid g = make_grid(H[j], W[j], 0);
+    tiles += g.n_tiles();
+    scratch += al256b(label_scratch_bytes(g));
+  }
+  if (n_tiles_out) *n_tiles_out = tiles;
+  return al256b((int64_t)sizeof(CclJob) * n) + al256b(4 * tiles) + scratch;
+}
+}  // namespace
+
+int64_t ccl_batch_workspace_bytes(int n, const int* H, const int* W) {
+  if (n < 0 || (n > 0 && (!H || !W))) return -1;
+  return ccl_batch_bytes(n, H, W, nullptr);
+}
+
+int ccl_label_batch(int n, const uint8_t* const* masks, int32_t* const* labels, const int* H, const int* W,
+                    const int* periodic, void* workspace, int64_t ws_bytes, void* stream) {
+  if (n < 0 || (n > 0 && (!masks || !labels || !H || !W || !periodic)))
+    return fail(SW_ERR_ARG, "ccl_label_batch: bad arguments");
+  if (n == 0) return SW_OK;
+  int64_t n_tiles = 0;
+  const int64_t need = ccl_batch_bytes(n, H, W, &n_tiles);
+  if (need < 0) return fail(SW_ERR_ARG, "ccl_label_batch: need H, W >= 1 and H*W < 2^31 for every grid");
+  if (!workspace || ws_bytes < need || ((uintptr_t)workspace & 255))
+    return fail(SW_ERR_ARG, "ccl_label_batch: workspace missing, smaller than ccl_batch_workspace_bytes or not "
+                            "256-byte aligned");
+  if (n_tiles >= ((int64_t)1 << 31)) return fail(SW_ERR_ARG, "ccl_label_batch: too many tiles");
+  for (int j = 0; j < n; ++j)
+    if (!masks[j] || !labels[j]) return fail(SW_ERR_ARG, "ccl_label_batch: null mask or label pointer");
+  int* status = ccl_status_ptr();
+  if (!status) return fail(SW_ERR_CUDA, "ccl_label_batch: cannot resolve the device status word");
+  char* base = static_cast<char*>(workspace);
+  CclJob* d_jobs = reinterpret_cast<CclJob*>(base);
+  int* d_tile_job = reinterpret_cast<int*>(base + al256b((int64_t)sizeof(CclJob) * n));
+  char* p = base + al256b((int64_t)sizeof(CclJob) * n) + al256b(4 * n_tiles);
+  std::vector<CclJob> jobs(n);
+  std::vector<int> tile_job((size_t)n_tiles);
+  int t0 = 0;
+  int64_t max_sites = 0;
+  for (int j = 0; j < n; ++j) {
+    const Grid g = make_grid(H[j], W[j], periodic[j]);
+    jobs[j].mask = masks[j];
+    jobs[j].labels = labels[j];
+    jobs[j].s = carve_label_scratch(g, p, status);
+    jobs[j].g = g;
+    jobs[j].tile0 = t0;
+    jobs[j].pad = 0;
+    p += al256b(label_scratch_bytes(g));
+    for (int k = 0; k < g.n_tiles(); ++k) tile_job[t0 + k] = j;
+    t0 += g.n_tiles();
+    max_sites = std::max<int64_t>(max_sites, g.n_sites());
+  }
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // pageable sources: the copies complete before these calls return
+  CK(cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(CclJob) * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_tile_job, tile_job.data(), sizeof(int) * n_tiles, cudaMemcpyHostToDevice, st));
+  CclBatchView v;
+  v.jobs = d_jobs;
+  v.tile_job = d_tile_job;
+  v.n_jobs = n;
+  v.n_tiles = (int)n_tiles;
+  v.limit = (int)std::min<int64_t>(max_sites + 64, (int64_t)1 << 30);
+  v.pad = 0;
+  CK(launch_ccl_batch(v, st));
   return SW_OK;
 }
 

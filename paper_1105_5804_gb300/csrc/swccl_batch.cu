@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstddef>
+#include <cstdint>
 #include <string>
 #include <vector>
 
@@ -20,11 +21,6 @@ namespace {
 constexpr int BATCH_OBS_CAP = 4096;
 
 inline int64_t al256(int64_t b) { return (b + 255) & ~(int64_t)255; }
-
-double coupling(int q, double beta, double J, int conv) {
-  if (conv == SW_CONV_AUTO) conv = (q == 2) ? SW_CONV_ISING : SW_CONV_POTTS;
-  return conv == SW_CONV_ISING ? 2.0 * beta * J : beta * J;
-}
 }  // namespace
 
 struct sw_batch {

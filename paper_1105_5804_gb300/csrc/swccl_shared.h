@@ -104,6 +104,25 @@ struct BatchView {
   int limit;          // union-find step bound: largest replica's sites + 64
 };
 
+// One grid of a batched labeling call.
+struct CclJob {
+  const uint8_t* mask;
+  int32_t* labels;
+  LabelScratch s;
+  Grid g;
+  int tile0;          // first global tile of this grid
+  int pad;
+};
+
+struct CclBatchView {
+  const CclJob* jobs;
+  const int* tile_job;
+  int n_jobs;
+  int n_tiles;
+  int limit;          // union-find step bound: largest grid's sites + 64
+  int pad;
+};
+
 // Bytes of LabelScratch for a grid (each part 256-byte aligned).
 int64_t label_scratch_bytes(const Grid& g);
 LabelScratch carve_label_scratch(const Grid& g, void* base, int* err);
@@ -155,6 +174,9 @@ cudaError_t launch_batch_observe(const BatchView& b, BatchCtl* ctl, cudaStream_t
 cudaError_t launch_batch_persistent(const BatchView& b, BatchCtl* ctl, int blocks, cudaStream_t st);
 // Largest number of co-resident CTAs of the persistent kernel per SM.
 int batch_persistent_blocks_per_sm();
+
+// Batched labeling (k_ccl_batch.cu): the four steps over all tiles of all grids.
+cudaError_t launch_ccl_batch(const CclBatchView& v, cudaStream_t st);
 
 // Host helpers of the C ABI: set this thread's sw_last_error() message and
 // return `code`; device address of the stand-alone labeling status word on

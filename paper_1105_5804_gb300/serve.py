@@ -1,0 +1,225 @@
+"""Serving loop: continuous batching of labeling and Swendsen-Wang jobs.
+
+Requests arrive over time (a Poisson stream in the benchmark).  Two kinds:
+
+* label: an H x W image of grey levels -> the canonical labels of its
+  4-neighbour equal-level clusters (open boundaries): the segmentation task the
+  paper names as an application of cluster identification (Sec. I);
+* sw:    an L x L Ising chain at a given beta -> n sweeps, their observables.
+
+The server keeps a FIFO queue and a fixed number of slots, each with its own
+CUDA stream.  On every step it admits queued jobs in arrival order while a
+slot is free and the job's device memory fits the HBM budget; the label jobs
+admitted in one step run as one ccl_label_batch call, the sw jobs as one
+sw_batch, each group on a free slot's stream, so newly admitted work overlaps
+on the GPU with work already running.  Completed groups (CUDA event queried,
+never waited on) release their slot and memory.  Results do not depend on
+what else ran: every job's computation reads only its own inputs and seed.
+
+All computation runs in the library's kernels; torch provides device memory
+(its caching allocator) and streams.
+"""
+import collections
+import time
+
+import numpy as np
+
+from . import _lib as sw
+
+LABEL_BYTES_PER_PX = 1 + 0.25 + 4          # pixels, packed mask, labels (+ workspace, counted exactly)
+SW_BYTES_PER_SITE = 15.8                    # handle memory of one chain
+
+
+class Job:
+    __slots__ = ("id", "kind", "arrival", "H", "W", "pixels", "L", "beta", "sweeps", "seed", "bytes",
+                 "t_admit", "t_done", "labels", "observables", "spins")
+
+    def __init__(self, jid, kind, arrival, **kw):
+        self.id, self.kind, self.arrival = jid, kind, arrival
+        self.H = kw.get("H")
+        self.W = kw.get("W")
+        self.pixels = kw.get("pixels")
+        self.L = kw.get("L")
+        self.beta = kw.get("beta")
+        self.sweeps = kw.get("sweeps", 10)
+        self.seed = kw.get("seed", jid)
+        if kind == "label":
+            self.bytes = int(self.H * self.W * LABEL_BYTES_PER_PX) + sw.ccl_batch_workspace_bytes([self.H], [self.W])
+        else:
+            self.bytes = int(self.L * self.L * SW_BYTES_PER_SITE) + 4096 * 3 * 8
+        self.t_admit = self.t_done = None
+        self.labels = self.observables = self.spins = None
+
+
+class _Group:
+    """Jobs launched together on one slot."""
+
+    def __init__(self, slot, jobs, kind):
+        self.slot, self.jobs, self.kind = slot, jobs, kind
+        self.event = None
+        self.keep = []          # device buffers alive until completion
+        self.batch = None       # sw_batch handle
+
+
+class Server:
+    def __init__(self, hbm_budget_bytes, slots=4, max_group=32, keep_results=False):
+        import torch
+        self.torch = torch
+        self.budget = int(hbm_budget_bytes)
+        self.in_use = 0
+        self.streams = [torch.cuda.Stream() for _ in range(slots)]
+        self.free_slots = list(range(slots))
+        self.max_group = max_group
+        self.keep_results = keep_results
+        self.queue = collections.deque()
+        self.running = []
+        self.done = []
+        self.peak_in_use = 0
+        self.max_running = 0
+
+    def submit(self, job):
+        self.queue.append(job)
+
+    def idle(self):
+        return not self.queue and not self.running
+
+    # -- admission -----------------------------------------------------------
+    def _admit(self, now):
+        """Admit queued jobs in arrival order: the label jobs of this step form
+        one group and the sw jobs another; a group needs a free slot; a job
+        needs its bytes within the budget.  The first job that does not fit
+        stops admission (first in, first out)."""
+        groups = {"label": [], "sw": []}
+        while self.queue:
+            job = self.queue[0]
+            if job.bytes > self.budget:
+                raise ValueError("job %d needs %d bytes, more than the whole budget" % (job.id, job.bytes))
+            grp = groups[job.kind]
+            opened = sum(1 for g in groups.values() if g)
+            if not grp and opened + 1 > len(self.free_slots):
+                break
+            if len(grp) >= self.max_group or self.in_use + job.bytes > self.budget:
+                break
+            self.queue.popleft()
+            self.in_use += job.bytes
+            job.t_admit = now
+            grp.append(job)
+        self.peak_in_use = max(self.peak_in_use, self.in_use)
+        for kind, jobs in groups.items():
+            if jobs:
+                self._launch(kind, jobs)
+
+    def _launch(self, kind, jobs):
+        torch = self.torch
+        slot = self.free_slots.pop()
+        st = self.streams[slot]
+        g = _Group(slot, jobs, kind)
+        with torch.cuda.stream(st):
+            if kind == "label":
+                masks, labels = [], []
+                for j in jobs:
+                    px = torch.from_numpy(np.ascontiguousarray(j.pixels).reshape(-1)).to("cuda", non_blocking=False)
+                    m = torch.empty(sw.mask_bytes(j.H * j.W), dtype=torch.uint8, device="cuda")
+                    sw.ccl_bonds_from_pixels(px, m, j.H, j.W, False, st)
+                    lab = torch.empty(j.H * j.W, dtype=torch.int32, device="cuda")
+                    masks.append(m)
+                    labels.append(lab)
+                    g.keep += [px, m]
+                ws = torch.empty(sw.ccl_batch_workspace_bytes([j.H for j in jobs], [j.W for j in jobs]),
+                                 dtype=torch.uint8, device="cuda")
+                g.keep.append(ws)
+                sw.ccl_label_batch(masks, labels, [j.H for j in jobs], [j.W for j in jobs], [False] * len(jobs),
+                                   ws, st)
+                for j, lab in zip(jobs, labels):
+                    j.labels = lab
+            else:
+                b = sw.sw_batch_create([j.L for j in jobs], [2] * len(jobs), [j.beta for j in jobs],
+                                       [j.seed for j in jobs], sw.SW_CONV_ISING, True, st)
+                g.batch = b
+                n = max(j.sweeps for j in jobs)
+                sw.sw_batch_sweep(b, n)
+            g.event = torch.cuda.Event()
+            g.event.record(st)
+        self.running.append(g)
+        self.max_running = max(self.max_running, len(self.running))
+
+    # -- completion ----------------------------------------------------------
+    def _collect(self, now):
+        still = []
+        for g in self.running:
+            if not g.event.query():
+                still.append(g)
+                continue
+            if g.kind == "sw":
+                for r, j in enumerate(g.jobs):
+                    j.observables = sw.sw_batch_observables(g.batch, r, 2)[: j.sweeps]
+                    if self.keep_results:
+                        j.spins = sw.sw_batch_get_spins(g.batch, r, j.L)
+                sw.sw_batch_destroy(g.batch)
+            else:
+                if not self.keep_results:
+                    for j in g.jobs:
+                        j.labels = None
+            for j in g.jobs:
+                j.t_done = now
+                j.pixels = None
+                self.in_use -= j.bytes
+                self.done.append(j)
+            self.free_slots.append(g.slot)
+        self.running = still
+
+    def step(self, now):
+        self._collect(now)
+        self._admit(now)
+
+
+def make_jobs(rate, n_jobs, seed=0, label_fraction=0.8, hw=(256, 8192), sw_L=(128, 4096), image_pool=None,
+              sweeps=10, beta=0.5 * np.log(1 + np.sqrt(2.0))):
+    """A Poisson stream of n_jobs requests at `rate` per second.  Label jobs
+    take H, W uniform in hw and their pixels are windows of `image_pool` (a
+    large blurred-noise image of grey levels); sw jobs take L uniform in sw_L
+    (multiple of 4), the given beta, seed = job id."""
+    from .inputs import poisson_arrivals
+    rng = np.random.default_rng(seed)
+    t = poisson_arrivals(rate, n_jobs, seed)
+    jobs = []
+    for k in range(n_jobs):
+        if rng.random() < label_fraction:
+            H = int(rng.integers(hw[0], hw[1] + 1))
+            W = int(rng.integers(hw[0], hw[1] + 1))
+            y = int(rng.integers(0, image_pool.shape[0] - H + 1))
+            x = int(rng.integers(0, image_pool.shape[1] - W + 1))
+            jobs.append(Job(k, "label", float(t[k]), H=H, W=W, pixels=image_pool[y:y + H, x:x + W]))
+        else:
+            L = 4 * int(rng.integers(sw_L[0] // 4, sw_L[1] // 4 + 1))
+            jobs.append(Job(k, "sw", float(t[k]), L=L, beta=beta, sweeps=sweeps, seed=k))
+    return jobs
+
+
+def run(jobs, server, time_scale=1.0):
+    """Feed jobs at their arrival times (seconds from now x time_scale) and
+    step the server until all are done.  Returns the completed jobs."""
+    torch = server.torch
+    t0 = time.perf_counter()
+    pending = collections.deque(sorted(jobs, key=lambda j: j.arrival))
+    while pending or not server.idle():
+        now = time.perf_counter() - t0
+        while pending and pending[0].arrival * time_scale <= now:
+            server.submit(pending.popleft())
+        server.step(now)
+        if not server.running and not server.queue and pending:
+            wait = pending[0].arrival * time_scale - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(min(wait, 0.002))
+    torch.cuda.synchronize()
+    sw.ccl_status()             # device-side failures of any labeling group
+    return server.done
+
+
+def summary(done, time_scale=1.0):
+    lat = np.array([j.t_done - j.arrival * time_scale for j in done])
+    span = max(j.t_done for j in done) - min(j.arrival * time_scale for j in done)
+    sites = sum((j.H * j.W) if j.kind == "label" else (j.L * j.L * j.sweeps) for j in done)
+    return {"jobs": len(done), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3), "jobs_per_s": len(done) / span,
+            "gsite_updates_per_s": sites / span / 1e9}

@@ -168,3 +168,38 @@ def test_labeling_workload_4096_seeds():
         dens.append(n_roots / (H * W))
     import oracle.exact as ex
     assert abs(np.mean(dens) - ex.PERC_CLUSTER_DENSITY) < 2e-4
+
+
+def test_label_batch_mixed_grids_equal_oracle_and_single_calls():
+    """ccl_label_batch over grids of different sizes, densities and boundary
+    conditions (one launch per step for all): every grid's labels equal the
+    oracle's and those of ccl_label alone."""
+    rng = np.random.default_rng(17)
+    shapes = [(1, 1), (3, 5), (64, 256), (65, 257), (200, 300), (1000, 7), (7, 1000), (333, 444), (2048, 300)]
+    masks, labs, H, W, P, refs = [], [], [], [], [], []
+    for j, (h, w) in enumerate(shapes):
+        periodic = bool(j % 2)
+        p = float(rng.choice([0.3, 0.5, 0.62, 0.9]))
+        m = inputs.random_mask(h, w, p, seed=50 + j)
+        masks.append(_dev(m))
+        labs.append(torch.full((h * w,), -1, dtype=torch.int32, device="cuda"))
+        H.append(h); W.append(w); P.append(periodic)
+        refs.append(oracle.label(m, h, w, periodic)[0])
+    ws = torch.empty(sw.ccl_batch_workspace_bytes(H, W), dtype=torch.uint8, device="cuda")
+    for _ in range(2):            # the second call reuses the workspace
+        for lab in labs:
+            lab.fill_(-1)
+        sw.ccl_label_batch(masks, labs, H, W, P, ws)
+        sw.ccl_status()
+        for j in range(len(shapes)):
+            got = labs[j].cpu().numpy()
+            assert np.array_equal(got, refs[j]), shapes[j]
+            assert np.array_equal(got, _gpu_label(masks[j].cpu().numpy(), H[j], W[j], P[j]))
+
+
+def test_label_batch_rejects_small_workspace():
+    ws = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    m = torch.zeros(sw.mask_bytes(64 * 64), dtype=torch.uint8, device="cuda")
+    lab = torch.zeros(64 * 64, dtype=torch.int32, device="cuda")
+    with pytest.raises(sw.SwcclError):
+        sw.ccl_label_batch([m], [lab], [64], [64], [True], ws)
