@@ -300,6 +300,29 @@ def batch_secondary(torch, sw, sweeps=50, single_sweeps=5):
     return res
 
 
+def serving_secondary(torch, rates=(10, 30, 100, 300, 1000, 2000), seconds=1.0, max_jobs=400):
+    """The serving workload: a Poisson stream of segmentation jobs (H, W
+    uniform in [256, 8192], windows of a blurred-noise 8-level image) and SW
+    jobs (L uniform in [128, 4096], 10 sweeps at the Ising beta_c), 80:20,
+    through the continuous-batching server with a 64 GiB budget and 4 slots.
+    Latency = completion (results on the device) - arrival."""
+    from paper_1105_5804_gb300 import inputs, serve
+    pool = inputs.blurred_noise_image(8192, 8192, seed=0)
+    out = {"workload": "serve_label_HW256-8192_sw_L128-4096_poisson", "budget_gib": 64, "slots": 4, "rates": {}}
+    # warm-up: allocator, graphs, libraries
+    serve.run(serve.make_jobs(1000.0, 8, seed=99, image_pool=pool), serve.Server(64 << 30, slots=4))
+    for rate in rates:
+        n = int(min(max_jobs, max(20, rate * seconds)))
+        jobs = serve.make_jobs(float(rate), n, seed=0, image_pool=pool)
+        srv = serve.Server(64 << 30, slots=4)
+        done = serve.run(jobs, srv)
+        res = serve.summary(done)
+        res["max_concurrent_groups"] = srv.max_running
+        res["peak_hbm_gib"] = srv.peak_in_use / 2 ** 30
+        out["rates"][str(rate)] = res
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -388,6 +411,7 @@ def run_ours(args):
                                            "unit": "site-updates/ns", "beta": math.log(3.0), "sweeps": 50}
         sw.sw_destroy(h4)
         secondary["batch_512"] = batch_secondary(torch, sw)
+        secondary["serving"] = serving_secondary(torch)
     sw.sw_destroy(h)
 
     if rank != 0:
