@@ -10,22 +10,40 @@ namespace swccl {
 namespace fused {
 
 // Four byte lanes of a and b compared: bit k of the result is set iff byte k
-// of a equals byte k of b.
+// of a equals byte k of b.  Exact zero-byte test of a ^ b (no carry crosses a
+// byte: each byte of (x & 0x7F..) + 0x7F.. is at most 0xFE), then the four
+// flag bits are gathered by one multiply.
 __device__ __forceinline__ uint32_t eq4(uint32_t a, uint32_t b) {
-  const uint32_t m = __vcmpeq4(a, b);               // 0xFF per equal byte
-  return ((m & 0x08040201u) * 0x01010101u) >> 24;   // gather one bit per byte
+  const uint32_t x = a ^ b;
+  const uint32_t y = ((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x;   // bit 7 of a byte set iff the byte is non-zero
+  const uint32_t z = (~y & 0x80808080u) >> 7;                  // bit 0 of a byte set iff equal
+  return (z * 0x00204081u) >> 21 & 0xFu;
 }
 
-// Bonds (and observable counts) of 32 consecutive sites of one row.
+// Spread the 32 bits of v to the even bits of a 64-bit word.
+__device__ __forceinline__ unsigned long long spread_even(uint32_t v) {
+  unsigned long long x = v;
+  x = (x | (x << 16)) & 0x0000FFFF0000FFFFull;
+  x = (x | (x << 8)) & 0x00FF00FF00FF00FFull;
+  x = (x | (x << 4)) & 0x0F0F0F0F0F0F0F0Full;
+  x = (x | (x << 2)) & 0x3333333333333333ull;
+  x = (x | (x << 1)) & 0x5555555555555555ull;
+  return x;
+}
+
+// Bonds of 32 consecutive sites of one row, and the observables of the
+// spins read (bonds joining equal spins; sites per state for q <= QREG).
 struct RowBonds {
   unsigned long long word;  // bit 2i east bond, 2i+1 north bond (rule of Eq. 7)
-  uint32_t eq_e, eq_n;      // site i equals its east / north neighbour
+  int n_eq;                 // equal east and north neighbours among the sites
+  int cnt[8];               // sites per state (q <= 8)
 };
 
-__device__ __forceinline__ RowBonds row_bonds(const int8_t* __restrict__ spins, int L, int y, int x, int nvalid,
-                                              uint64_t T, uint32_t klo, uint32_t khi, uint32_t sw_lo,
-                                              uint32_t sw_hi) {
-  RowBonds rb{0ull, 0u, 0u};
+constexpr int QREG_MAX = 8;
+
+__device__ __forceinline__ void row_bonds(const int8_t* __restrict__ spins, int L, int y, int x, int nvalid,
+                                          uint64_t T, uint32_t klo, uint32_t khi, uint32_t sw_lo, uint32_t sw_hi,
+                                          int q, RowBonds& rb) {
   const int yn = (y + 1 == L) ? 0 : y + 1;
   const int64_t row = (int64_t)y * L, rown = (int64_t)yn * L;
   uint32_t s[8], n[8];
@@ -46,47 +64,56 @@ __device__ __forceinline__ RowBonds row_bonds(const int8_t* __restrict__ spins, 
   }
   const int xe = (x + nvalid == L) ? 0 : x + nvalid;
   const uint32_t east_byte = (uint32_t)(uint8_t)spins[row + xe];
+  uint32_t eq_e = 0, eq_n = 0;
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     if (k < nw) {
       const uint32_t next = (k + 1 < nw) ? s[k + 1] : east_byte;
-      const uint32_t e = (s[k] >> 8) | (next << 24);
-      rb.eq_e |= eq4(s[k], e) << (4 * k);
-      rb.eq_n |= eq4(s[k], n[k]) << (4 * k);
+      eq_e |= eq4(s[k], (s[k] >> 8) | (next << 24)) << (4 * k);
+      eq_n |= eq4(s[k], n[k]) << (4 * k);
     }
   }
-  const bool all_open = T >= (1ull << 32);
-  const uint32_t thr = (uint32_t)T;
-  const uint32_t eq = rb.eq_e | rb.eq_n;
+  // observables of the spins read
+  const uint32_t valid = nvalid == 32 ? 0xFFFFFFFFu : ((1u << nvalid) - 1u);
+  rb.n_eq = __popc(eq_e & valid) + __popc(eq_n & valid);
 #pragma unroll
-  for (int i = 0; i < 32; i += 2) {
-    if (i >= nvalid) break;
-    const uint32_t need = (eq >> i) & 3u;
-    if (!need) continue;
-    const uint32_t e0 = (rb.eq_e >> i) & 1u, n0 = (rb.eq_n >> i) & 1u;
-    const uint32_t e1 = (rb.eq_e >> (i + 1)) & 1u, n1 = (rb.eq_n >> (i + 1)) & 1u;
-    uint32_t bits;
-    if (all_open) {
-      bits = e0 | (n0 << 1) | (e1 << 2) | (n1 << 3);
-    } else if (thr == 0) {
-      bits = 0;
-    } else {
-      const uint4 r = philox(make_uint4((uint32_t)((row + x + i) >> 1), sw_lo, sw_hi, TAG_BOND), klo, khi);
-      bits = (e0 & (r.x < thr)) | ((n0 & (r.y < thr)) << 1) | ((e1 & (r.z < thr)) << 2) | ((n1 & (r.w < thr)) << 3);
+  for (int c = 0; c < QREG_MAX; ++c) rb.cnt[c] = 0;
+  if (q == 2) {
+    int ones = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) ones += (k < nw) ? __popc(s[k] & 0x01010101u) : 0;
+    rb.cnt[0] = nvalid - ones;
+    rb.cnt[1] = ones;
+  } else if (q <= QREG_MAX) {
+#pragma unroll
+    for (int c = 0; c < QREG_MAX; ++c) {
+      if (c >= q) break;
+      int m = 0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) m += (k < nw) ? __popc(eq4(s[k], 0x01010101u * (uint32_t)c)) : 0;
+      rb.cnt[c] = m;
     }
-    rb.word |= (unsigned long long)bits << (2 * i);
   }
-  return rb;
+  // bonds: site i's east bit at 2i, north bit at 2i+1; one Philox call per pair
+  const unsigned long long eqw = spread_even(eq_e) | (spread_even(eq_n) << 1);
+  if (T >= (1ull << 32)) {
+    rb.word = eqw;                       // p = 1: every bond between equal spins opens
+  } else if (T == 0) {
+    rb.word = 0ull;
+  } else {
+    const uint32_t thr = (uint32_t)T;
+    unsigned long long word = 0ull;
+#pragma unroll
+    for (int i = 0; i < 32; i += 2) {
+      if (i >= nvalid) break;
+      const uint4 r = philox(make_uint4((uint32_t)((row + x + i) >> 1), sw_lo, sw_hi, TAG_BOND), klo, khi);
+      const uint32_t c = (uint32_t)(r.x < thr) | ((uint32_t)(r.y < thr) << 1) | ((uint32_t)(r.z < thr) << 2) |
+                         ((uint32_t)(r.w < thr) << 3);
+      word |= (unsigned long long)c << (2 * i);
+    }
+    rb.word = word & eqw;
+  }
 }
-
-// Number of sites in state k among the first nvalid bytes of s (k < q).
-__device__ __forceinline__ int count_state(const int8_t* __restrict__ p, int nvalid, int k) {
-  int c = 0;
-  for (int j = 0; j < nvalid; j += 4) c += __popc(eq4(*reinterpret_cast<const uint32_t*>(p + j), 0x01010101u * (uint32_t)k));
-  return c;
-}
-
-constexpr int QREG_MAX = 8;
 
 // Block-wide sums of n_eq and the state counts, added to the observable slot.
 template <int NTHREADS>
@@ -176,8 +203,9 @@ __device__ __forceinline__ void sw_label_tile(const SwRep& R, int t, uint64_t sw
     unsigned long long wd = 0ull;
     if (ly < h && nvalid > 0) {
       const int y = y0 + ly, x = x0 + 32 * c;
-      const RowBonds rb = row_bonds(spins, L, y, x, nvalid, T, (uint32_t)seed, (uint32_t)(seed >> 32),
-                                    (uint32_t)sweep, (uint32_t)(sweep >> 32));
+      RowBonds rb;
+      row_bonds(spins, L, y, x, nvalid, T, (uint32_t)seed, (uint32_t)(seed >> 32), (uint32_t)sweep,
+                (uint32_t)(sweep >> 32), q, rb);
       wd = rb.word;
       if (32 * c + nvalid == w) {                 // east bond leaving the tile
         const int bit = 2 * (nvalid - 1);
@@ -185,14 +213,12 @@ __device__ __forceinline__ void sw_label_tile(const SwRep& R, int t, uint64_t sw
         wd &= ~(1ull << bit);
       }
       if (do_obs) {
-        const uint32_t valid = nvalid == 32 ? 0xFFFFFFFFu : ((1u << nvalid) - 1u);
-        n_eq = __popc(rb.eq_e & valid) + __popc(rb.eq_n & valid);
-        const int8_t* p = spins + (int64_t)y * L + x;
+        n_eq = rb.n_eq;
         if (q <= QREG) {
 #pragma unroll
-          for (int k = 0; k < QREG; ++k)
-            if (k < q) cnt[k] = count_state(p, nvalid, k);
+          for (int k = 0; k < QREG; ++k) cnt[k] = rb.cnt[k];
         } else {
+          const int8_t* p = spins + (int64_t)y * L + x;
           for (int j = 0; j < nvalid; ++j) atomicAdd(&hist[p[j]], 1);
         }
       }
