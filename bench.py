@@ -228,6 +228,42 @@ def ccl_secondary(torch, sw, n_seeds=20):
             "l2": "flushed (256 MiB write) between labels"}
 
 
+# The rows of the paper's benchmark table (Table I) at L = 8192: q, beta/beta_c
+# (delta convention, beta_c = ln(1 + sqrt q)), and the paper's GPU time per
+# site and sweep on a GTX 480 with self-labeling and sewing (context only).
+TABLE_ROWS = ((2, 1.0, 3.179), (2, 0.6, 1.863), (2, 1.4, 4.164), (3, 1.0, 3.059), (4, 1.0, 2.887))
+
+
+def table_secondary(torch, sw, L=8192, warm=100, sweeps=100):
+    """The paper's table variants: fused sweeps of an L = 8192 lattice, hot
+    start seed 7, after `warm` sweeps (the ordered phase has formed at 1.4
+    beta_c), timed with events on the handle's stream."""
+    out = {}
+    for q, ratio, paper_ns in TABLE_ROWS:
+        beta = ratio * math.log(1.0 + math.sqrt(q))
+        h = sw.sw_create_ex(L, q, beta, 1.0, sw.SW_CONV_POTTS, SEED_BENCH, True)
+        try:
+            sw.sw_sweep(h, warm)
+            st = torch.cuda.ExternalStream(sw.sw_stream(h))
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            sw.sw_sweep(h, sweeps)
+            b.record(st)
+            torch.cuda.synchronize()
+            obs = sw.sw_observables(h, 4096)
+            ms = a.elapsed_time(b)
+            out["q%d_beta%.1f" % (q, ratio)] = {
+                "value": L * L * sweeps / (ms * 1e6), "unit": "site-updates/ns", "ms_per_sweep": ms / sweeps,
+                "beta": beta, "mean_n_eq_per_site": float(obs[-sweeps:, 0].mean()) / (L * L),
+                "paper_gtx480_ns_per_site": paper_ns}
+        finally:
+            sw.sw_destroy(h)
+    return {"workload": "sw_potts_L8192_hot_start_seed7_table_rows", "warmup_sweeps": warm, "sweeps": sweeps,
+            "rows": out}
+
+
 def philox_ceiling(torch, sw, reps=3):
     """Measured integer-ALU ceiling: Philox4x32-10 calls per second of a
     kernel that does nothing else, 8 CTAs x 256 threads per SM on every SM."""
@@ -410,6 +446,7 @@ def run_ours(args):
         secondary["sw_potts_q4_L16384"] = {"value": N * 50 / (a.elapsed_time(b) * 1e6),
                                            "unit": "site-updates/ns", "beta": math.log(3.0), "sweeps": 50}
         sw.sw_destroy(h4)
+        secondary["table_L8192"] = table_secondary(torch, sw)
         secondary["batch_512"] = batch_secondary(torch, sw)
         secondary["serving"] = serving_secondary(torch)
     sw.sw_destroy(h)

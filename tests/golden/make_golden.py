@@ -45,6 +45,21 @@ def main():
     with open(os.path.join(HERE, "ising_exact_beta_c.json"), "w") as f:
         json.dump(ising, f, indent=1)
 
+    # 1b. The same moments off criticality, at the beta / beta_c ratios of the
+    #     paper's benchmark table (Sec. III, Table I: 0.6 and 1.4 for q = 2).
+    off = {
+        "citation": "Weigel arXiv:1105.5804 Table I (beta/beta_c = 0.6, 1.4 for q = 2); formula: Kaufman 1949",
+        "convention": "as ising_exact_beta_c.json, with K = ratio * ln(1+sqrt2)/2",
+        "L": 16,
+        "ratios": {},
+    }
+    for ratio in (0.6, 1.4):
+        K = ratio * KC_ISING
+        S, varS = ex.ising_torus_energy_moments(16, K)
+        off["ratios"][str(ratio)] = {"K": K, "mean_n_eq": (S + 2 * 256) / 2.0, "var_n_eq": varS / 4.0}
+    with open(os.path.join(HERE, "ising_exact_off_critical.json"), "w") as f:
+        json.dump(off, f, indent=1)
+
     # 2. Exact density of states of the q-state Potts model on the 4 x 4 torus.
     dos = {
         "citation": "Potts Hamiltonian, Weigel arXiv:1105.5804 Sec. II Eq. 1; row transfer matrix "

@@ -111,3 +111,42 @@ def test_ising_energy_and_specific_heat_against_exact_torus(L, n_sweeps, hot, se
     assert abs(m - ref["mean_n_eq"]) < Z_TOL * e, (m, ref["mean_n_eq"], e)
     var, verr = _jackknife_var(n)
     assert abs(var - ref["var_n_eq"]) < Z_TOL * verr, (var, ref["var_n_eq"], verr)
+
+
+# ---------------------------------------------------------------------------
+# Off criticality: the beta / beta_c ratios of the paper's benchmark table
+# (Table I: 0.6 and 1.4 for q = 2; q = 3 at the same ratios here).
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("ratio", [0.6, 1.4])
+def test_ising_4x4_off_critical_against_enumeration(ratio):
+    K, obs = _run(4, 2, ratio * KC_ISING, oracle.CONV_ISING, seed=31, n_sweeps=200_000)
+    n_eq, counts = ex.enumerate_potts(4, 4, 2)
+    exact = ex.moments_from_states(n_eq, counts, K, 2)
+    n = obs[:, 0]
+    absM = np.abs(obs[:, 1] - obs[:, 2])
+    for series, key in ((n, "n_eq"), (n.astype(np.float64) ** 2, "n_eq2"), (absM, "absM")):
+        m, e, _ = _binned(series)
+        assert abs(m - exact[key]) < Z_TOL * e, (key, m, exact[key], e)
+
+
+@pytest.mark.parametrize("ratio", [0.6, 1.4])
+def test_potts_q3_4x4_off_critical_against_transfer_matrix(ratio):
+    K, obs = _run(4, 3, ratio * math.log(1 + math.sqrt(3)), oracle.CONV_POTTS, seed=41, n_sweeps=200_000)
+    g = np.array(json.load(open(os.path.join(GOLD, "potts_dos_4x4.json")))["g"]["3"])
+    exact = ex.dos_moments(g, K)
+    n = obs[:, 0].astype(np.float64)
+    for series, key in ((n, "n_eq"), (n * n, "n_eq2")):
+        m, e, _ = _binned(series)
+        assert abs(m - exact[key]) < Z_TOL * e, (key, m, exact[key], e)
+
+
+@pytest.mark.parametrize("ratio", [0.6, 1.4])
+def test_ising_16x16_off_critical_against_exact_torus(ratio):
+    ref = json.load(open(os.path.join(GOLD, "ising_exact_off_critical.json")))["ratios"][str(ratio)]
+    K, obs = _run(16, 2, ratio * KC_ISING, oracle.CONV_ISING, seed=17, n_sweeps=60_000, burn=200)
+    assert abs(K - 2 * ref["K"]) < 1e-15                # FK coupling = 2 x Ising coupling
+    n = obs[:, 0]
+    m, e, _ = _binned(n)
+    assert abs(m - ref["mean_n_eq"]) < Z_TOL * e, (m, ref["mean_n_eq"], e)
+    var, verr = _jackknife_var(n)
+    assert abs(var - ref["var_n_eq"]) < Z_TOL * verr, (var, ref["var_n_eq"], verr)
