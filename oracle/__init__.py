@@ -20,7 +20,7 @@ import numpy as np
 
 from . import build as _build
 
-TAG_BOND, TAG_FLIP, TAG_INIT, TAG_PERC = 0, 1, 2, 3
+TAG_BOND, TAG_FLIP, TAG_INIT, TAG_PERC, TAG_SEED = 0, 1, 2, 3, 4
 CONV_AUTO, CONV_POTTS, CONV_ISING = 0, 1, 2
 
 _lib = None
@@ -64,6 +64,16 @@ def lib():
         L.or_chain.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
         L.or_chain.restype = ctypes.c_int
+        L.or_few_seed.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64]
+        L.or_few_seed.restype = ctypes.c_int64
+        L.or_few_sweep.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
+                                   ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_void_p]
+        L.or_few_sweep.restype = ctypes.c_int
+        L.or_few_chain.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
+                                   ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64, ctypes.c_void_p,
+                                   ctypes.c_void_p]
+        L.or_few_chain.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -183,6 +193,37 @@ def chain(L: int, q: int, T: int, seed: int, sweep0: int, n_sweeps: int, spins):
     rc = lib().or_chain(L, q, T, seed, sweep0, n_sweeps, _ptr(s), _ptr(obs))
     if rc != 0:
         raise MemoryError("oracle chain failed")
+    return s, obs
+
+
+# --------------------------------------------------------------------------
+# Few-cluster update (Sec. IV, variant (c) of the single-cluster algorithm)
+# --------------------------------------------------------------------------
+def few_seed(L: int, ell: int, seed: int, sweep_index: int, b: int) -> int:
+    """Seed site of block b of the ell x ell block grid at this sweep."""
+    return int(lib().or_few_seed(L, ell, seed, sweep_index, b))
+
+
+def few_sweep(L: int, q: int, T: int, P: int, ell: int, seed: int, sweep_index: int, spins):
+    """One few-cluster sweep (flip threshold P).  Returns (new spins, mask,
+    canonical labels, observables)."""
+    s = _c(spins, np.int8).reshape(-1).copy()
+    m = np.zeros(mask_bytes(L * L), dtype=np.uint8)
+    lab = np.empty(L * L, dtype=np.int32)
+    obs = np.zeros(1 + q, dtype=np.int64)
+    rc = lib().or_few_sweep(L, q, T, P, ell, seed, sweep_index, _ptr(s), _ptr(m), _ptr(lab), _ptr(obs))
+    if rc != 0:
+        raise ValueError("oracle few-cluster sweep failed (ell must divide L)")
+    return s, m, lab, obs
+
+
+def few_chain(L: int, q: int, T: int, P: int, ell: int, seed: int, sweep0: int, n_sweeps: int, spins):
+    """n_sweeps few-cluster sweeps from sweep0.  Returns (final spins, obs)."""
+    s = _c(spins, np.int8).reshape(-1).copy()
+    obs = np.zeros((n_sweeps, 1 + q), dtype=np.int64)
+    rc = lib().or_few_chain(L, q, T, P, ell, seed, sweep0, n_sweeps, _ptr(s), _ptr(obs))
+    if rc != 0:
+        raise ValueError("oracle few-cluster chain failed (ell must divide L)")
     return s, obs
 
 

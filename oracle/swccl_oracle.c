@@ -32,16 +32,29 @@
  *       tag 1 FLIP: c0 = root site index, word 0
  *       tag 2 INIT: c0 = i, word 0, sweep 0
  *       tag 3 PERC: key = (k, 0), sweep 0, word mapping as BOND
+ *       tag 4 SEED: c0 = seed block index (few-cluster update), words 0, 1
  *   - a bond between equal spins is open iff (uint64)r < T,
  *     T = min(2^32, floor(p * 2^32))
  *   - new cluster state F_q(w) = floor(w * q / 2^32)
+ *
+ * The few-cluster update (Sec. IV, variant (c) of the single-cluster
+ * algorithm) is the SW decomposition followed by: one seed site per block of
+ * an ell x ell block grid (block side B = L / ell; the paper's tiles), every
+ * cluster holding a seed is selected, and each selected cluster flips with
+ * probability p_flip.  Readings where the paper is silent:
+ *   - seed of block b = by*ell + bx: SEED draw (b, sweep), x = bx*B + F_B(w0),
+ *     y = by*B + F_B(w1)
+ *   - the cluster with root R flips iff (uint64)w1 < P, w = FLIP draw of R,
+ *     P = min(2^32, floor(p_flip * 2^32)); its new state is
+ *     (s + 1 + F_{q-1}(w0)) mod q, a uniform choice among the other q - 1
+ *     states (for q = 2: s -> 1 - s, the paper's flip)
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
-enum { OR_TAG_BOND = 0, OR_TAG_FLIP = 1, OR_TAG_INIT = 2, OR_TAG_PERC = 3 };
+enum { OR_TAG_BOND = 0, OR_TAG_FLIP = 1, OR_TAG_INIT = 2, OR_TAG_PERC = 3, OR_TAG_SEED = 4 };
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10, written from the SC'11 description.                        */
@@ -301,6 +314,62 @@ int or_chain(int L, int q, uint64_t T, uint64_t seed, uint64_t sweep0, int64_t n
     for (int64_t s = 0; s < n_sweeps && rc == 0; s++)
         rc = or_sweep(L, q, T, seed, sweep0 + (uint64_t)s, spins, mask, labels,
                       obs ? obs + s * (1 + q) : NULL);
+    free(mask);
+    free(labels);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Few-cluster update (Sec. IV, variant (c)): SW bonds and clusters, then    */
+/* only the clusters of one seed per block flip, each with probability P.    */
+/* ------------------------------------------------------------------------ */
+/* Seed site of block b (0 <= b < ell*ell) at this sweep. */
+int64_t or_few_seed(int L, int ell, uint64_t seed, uint64_t sweep, int64_t b)
+{
+    int B = L / ell;
+    int64_t by = b / ell, bx = b % ell;
+    int64_t x = bx * B + or_flip_state(draw_word(seed, (uint32_t)b, sweep, OR_TAG_SEED, 0), B);
+    int64_t y = by * B + or_flip_state(draw_word(seed, (uint32_t)b, sweep, OR_TAG_SEED, 1), B);
+    return y * L + x;
+}
+
+/* spins updated in place; mask, labels as or_sweep.  Requires ell >= 1 and
+ * L % ell == 0.  Returns 0, or -1 on failure. */
+int or_few_sweep(int L, int q, uint64_t T, uint64_t P, int ell, uint64_t seed, uint64_t sweep, int8_t* spins,
+                 uint8_t* mask, int32_t* labels, int64_t* obs)
+{
+    int64_t N = (int64_t)L * L;
+    if (ell < 1 || L % ell != 0) return -1;
+    or_activate(L, spins, seed, sweep, T, mask);
+    if (or_label(L, L, 1, mask, labels) < 0) return -1;
+    uint8_t* selected = (uint8_t*)calloc((size_t)N, 1);
+    if (!selected) return -1;
+    for (int64_t b = 0; b < (int64_t)ell * ell; b++)
+        selected[labels[or_few_seed(L, ell, seed, sweep, b)]] = 1;
+    for (int64_t i = 0; i < N; i++) {
+        uint32_t root = (uint32_t)labels[i];
+        if (!selected[root]) continue;
+        uint32_t accept = draw_word(seed, root, sweep, OR_TAG_FLIP, 1);
+        if ((uint64_t)accept >= P) continue;
+        int shift = 1 + or_flip_state(draw_word(seed, root, sweep, OR_TAG_FLIP, 0), q - 1);
+        spins[i] = (int8_t)((spins[i] + shift) % q);
+    }
+    free(selected);
+    if (obs) or_observables(L, q, spins, obs);
+    return 0;
+}
+
+int or_few_chain(int L, int q, uint64_t T, uint64_t P, int ell, uint64_t seed, uint64_t sweep0, int64_t n_sweeps,
+                 int8_t* spins, int64_t* obs)
+{
+    int64_t N = (int64_t)L * L;
+    uint8_t* mask = (uint8_t*)malloc((size_t)or_mask_bytes(N));
+    int32_t* labels = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);
+    if (!mask || !labels) { free(mask); free(labels); return -1; }
+    int rc = 0;
+    for (int64_t s = 0; s < n_sweeps && rc == 0; s++)
+        rc = or_few_sweep(L, q, T, P, ell, seed, sweep0 + (uint64_t)s, spins, mask, labels,
+                          obs ? obs + s * (1 + q) : NULL);
     free(mask);
     free(labels);
     return rc;
