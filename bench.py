@@ -264,6 +264,33 @@ def table_secondary(torch, sw, L=8192, warm=100, sweeps=100):
             "rows": out}
 
 
+def few_cluster_secondary(torch, sw, L=L_BENCH, ells=(16, 256), p_flip=0.5, warm=20, sweeps=50):
+    """Few-cluster update (Sec. IV, variant (c)) on the benchmark lattice:
+    q = 2 at beta_c, hot start seed 7, one seed per block of an ell x ell
+    grid, seeded clusters flip with probability p_flip."""
+    out = {}
+    for ell in ells:
+        h = sw.sw_create_ex(L, Q_BENCH, KC_ISING, 1.0, sw.SW_CONV_ISING, SEED_BENCH, True)
+        try:
+            sw.sw_set_update(h, sw.SW_UPDATE_FEW, ell, sw.sw_prob_threshold(p_flip))
+            sw.sw_sweep(h, warm)
+            st = torch.cuda.ExternalStream(sw.sw_stream(h))
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            sw.sw_sweep(h, sweeps)
+            b.record(st)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            out["ell%d" % ell] = {"value": L * L * sweeps / (ms * 1e6), "unit": "site-updates/ns",
+                                  "ms_per_sweep": ms / sweeps, "seeds": ell * ell}
+        finally:
+            sw.sw_destroy(h)
+    return {"workload": "sw_few_cluster_ising_q2_L%d_beta_c_hot_start_seed7_pflip%.1f" % (L, p_flip),
+            "warmup_sweeps": warm, "sweeps": sweeps, "rows": out}
+
+
 def philox_ceiling(torch, sw, reps=3):
     """Measured integer-ALU ceiling: Philox4x32-10 calls per second of a
     kernel that does nothing else, 8 CTAs x 256 threads per SM on every SM."""
@@ -447,6 +474,7 @@ def run_ours(args):
                                            "unit": "site-updates/ns", "beta": math.log(3.0), "sweeps": 50}
         sw.sw_destroy(h4)
         secondary["table_L8192"] = table_secondary(torch, sw)
+        secondary["few_cluster"] = few_cluster_secondary(torch, sw)
         secondary["batch_512"] = batch_secondary(torch, sw)
         secondary["serving"] = serving_secondary(torch)
     sw.sw_destroy(h)

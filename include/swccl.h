@@ -182,6 +182,42 @@ int sw_set_timing(sw_handle* h, int enable);
 int sw_phase_times(sw_handle* h, double* ms, int64_t* n_sweeps);
 
 /* ------------------------------------------------------------------------ */
+/* Few-cluster update (Sec. IV, variant (c) of the single-cluster algorithm) */
+/* ------------------------------------------------------------------------ */
+
+/* The update a sweep applies after drawing the bonds and identifying the
+ * clusters (sw_set_update):
+ *   SW_UPDATE_SW (default): every cluster takes a new state (Sec. II.D);
+ *   SW_UPDATE_FEW: the few-cluster update.  The lattice is cut into an
+ *     ell x ell grid of blocks of side B = L / ell (the paper's tiles); each
+ *     sweep draws one seed site per block: for block b = by*ell + bx the
+ *     Philox draw w with counter (b, sweep_lo, sweep_hi, 4) gives
+ *     x = bx*B + F_B(w0), y = by*B + F_B(w1), F_m(v) = floor(v m / 2^32).
+ *     Every cluster holding at least one seed is selected; a selected
+ *     cluster with root R (its minimum site index) and FLIP draw v (as in
+ *     SW: counter (R, sweep_lo, sweep_hi, 1)) moves iff (uint64)v1 < P, from
+ *     its state s to (s + 1 + F_{q-1}(v0)) mod q (for q = 2: s -> 1 - s);
+ *     all other clusters keep their spins.  The bonds and clusters are those
+ *     of the SW sweep with the same arguments.  P = p_flip 2^32 (see
+ *     sw_prob_threshold); the paper asks p_flip < 1 for ergodicity, P = 2^32
+ *     (always flip) is accepted too.
+ * Cost: the SW sweep plus one warp per seed reading the seed tile's seam
+ * record (2.3 KB) and a memset of L*L/8 bytes; meant for few seeds
+ * (ell up to about L/32). */
+#define SW_UPDATE_SW 0
+#define SW_UPDATE_FEW 1
+
+/* Select the update of the following sweeps.  For SW_UPDATE_FEW: ell >= 1
+ * with L % ell == 0 and P <= 2^32 (ignored for SW_UPDATE_SW).  The few-
+ * cluster update runs in SW_MODE_FUSED only: SW_ERR_STATE in staged mode
+ * (and sw_set_mode(SW_MODE_STAGED) then fails likewise).  Allocates L*L/8
+ * bytes of device memory on first use.  Synchronises. */
+int sw_set_update(sw_handle* h, int update, int ell, uint64_t P);
+
+/* min(2^32, floor(p 2^32)) for p in [0, 1]; UINT64_MAX for p outside. */
+uint64_t sw_prob_threshold(double p);
+
+/* ------------------------------------------------------------------------ */
 /* Batches of independent chains (no counterpart in the paper: many         */
 /* replicas of uneven size and temperature advanced together)               */
 /* ------------------------------------------------------------------------ */

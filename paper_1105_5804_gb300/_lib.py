@@ -18,6 +18,7 @@ SW_CONV_AUTO, SW_CONV_POTTS, SW_CONV_ISING = 0, 1, 2
 SW_N_PHASES = 5
 SW_MODE_STAGED, SW_MODE_FUSED = 0, 1
 SW_BATCH_PHASES, SW_BATCH_PERSISTENT = 0, 1
+SW_UPDATE_SW, SW_UPDATE_FEW = 0, 1
 PHASE_NAMES = ("activate", "local", "merge", "roots", "flip")
 
 
@@ -57,6 +58,8 @@ def lib():
         "sw_stream": ([vp], vp),
         "sw_set_timing": ([vp, i32], i32),
         "sw_set_mode": ([vp, i32], i32),
+        "sw_set_update": ([vp, i32, i32, u64], i32),
+        "sw_prob_threshold": ([dbl], u64),
         "sw_phase_times": ([vp, vp, ctypes.POINTER(i64)], i32),
         "ccl_label": ([vp, vp, i32, i32, i32, vp], i32),
         "ccl_workspace_bytes": ([i32, i32], i64),
@@ -224,6 +227,14 @@ def sw_stream(h):
 
 def sw_set_mode(h, mode):
     _check(lib().sw_set_mode(h, mode))
+
+
+def sw_set_update(h, update, ell=0, P=0):
+    _check(lib().sw_set_update(h, update, ell, P))
+
+
+def sw_prob_threshold(p):
+    return int(lib().sw_prob_threshold(p))
 
 
 def sw_set_timing(h, enable):

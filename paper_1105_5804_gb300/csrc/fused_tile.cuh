@@ -280,7 +280,13 @@ __device__ __forceinline__ void sw_label_tile(const SwRep& R, int t, uint64_t sw
 
 // One tile of the fused flip step (see k_fused.cu).  All threads of the CTA
 // call it; it synchronises the CTA internally and on return.
-__device__ __forceinline__ void sw_flip_tile(const SwRep& R, int t, uint64_t sweep, int limit, FlipTileSmem& fs) {
+// FEW: the few-cluster update (Sec. IV, variant (c)).  Only clusters whose
+// global root has its bit set in `sel` (seeded clusters) move: with FLIP draw
+// w of the root, iff (uint64)w.y < P, to state (s + 1 + F_{q-1}(w.x)) mod q,
+// s being the cluster's current state (read at the tile root).
+template <bool FEW = false>
+__device__ __forceinline__ void sw_flip_tile(const SwRep& R, int t, uint64_t sweep, int limit, FlipTileSmem& fs,
+                                             const uint32_t* __restrict__ sel = nullptr, uint64_t P = 0) {
   // Thread t owns, in each of four passes j, the eight sites
   // (row 8j + t/32, columns 8(t%32) .. 8(t%32)+7) of the tile: one 16-byte
   // load of tile roots and one 8-byte store of spins per pass.
@@ -341,12 +347,17 @@ __device__ __forceinline__ void sw_flip_tile(const SwRep& R, int t, uint64_t swe
 #pragma unroll
   for (int j = 0; j < PASSES; ++j) {
     const int ly = 8 * j + warp;
+    const bool edge_row = ly == 0 || ly == h - 1;
+    int marked = -1;   // last root this lane marked (runs of equal roots along a row)
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int lx = lx0 + i;
       if (ly >= h || lx >= w) continue;
       const int r = root_of(j, i);
-      if (ly == 0 || ly == h - 1 || lx == 0 || lx == w - 1) atomicOr(&edge_mark[r >> 5], 1u << (r & 31));
+      if ((edge_row || lx == 0 || lx == w - 1) && r != marked) {
+        atomicOr(&edge_mark[r >> 5], 1u << (r & 31));
+        marked = r;
+      }
       if (r == ly * TILE_W + lx) mine |= 1u << (8 * j + i);
     }
   }
@@ -377,10 +388,21 @@ __device__ __forceinline__ void sw_flip_tile(const SwRep& R, int t, uint64_t swe
   const uint32_t klo = (uint32_t)seed, khi = (uint32_t)(seed >> 32);
   for (int k = threadIdx.x; k < n_roots; k += LABEL_THREADS) {
     const int r = rlist[k];
-    int R = tile_global(r, y0, x0, L);
-    if ((edge_mark[r >> 5] >> (r & 31)) & 1u) R = g_find(gpar, R, limit, err);
-    const uint4 d = philox(make_uint4((uint32_t)R, (uint32_t)sweep, (uint32_t)(sweep >> 32), TAG_FLIP), klo, khi);
-    ns[r] = (uint8_t)state_of(d.x, q);
+    int Rg = tile_global(r, y0, x0, L);
+    if ((edge_mark[r >> 5] >> (r & 31)) & 1u) Rg = g_find(gpar, Rg, limit, err);
+    if (FEW) {
+      // the cluster's current state, read at the tile root (this tile's own
+      // site: step 5 rewrites it only after a barrier)
+      int v = spins[(int64_t)(y0 + (r >> TILE_W_LOG2)) * L + x0 + (r & (TILE_W - 1))];
+      if ((__ldcg(sel + (Rg >> 5)) >> (Rg & 31)) & 1u) {
+        const uint4 d = philox(make_uint4((uint32_t)Rg, (uint32_t)sweep, (uint32_t)(sweep >> 32), TAG_FLIP), klo, khi);
+        if ((uint64_t)d.y < P) v = (v + 1 + state_of(d.x, q - 1)) % q;
+      }
+      ns[r] = (uint8_t)v;
+    } else {
+      const uint4 d = philox(make_uint4((uint32_t)Rg, (uint32_t)sweep, (uint32_t)(sweep >> 32), TAG_FLIP), klo, khi);
+      ns[r] = (uint8_t)state_of(d.x, q);
+    }
   }
   __syncthreads();
 
@@ -447,6 +469,40 @@ __device__ __forceinline__ void observe_tile(const SwRep& R, int t, uint64_t don
       reinterpret_cast<unsigned long long*>(R.obs + (int64_t)(done % (uint64_t)obs_cap) * (q + 1));
   add_observables<LABEL_THREADS>(n_eq, cnt, q, q <= QREG ? q : 0, oslot, ls.red, ls.hist);
   __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Few-cluster seed selection (Sec. IV, variant (c)): the seed of block b of
+// the ell x ell block grid (side B = L / ell) is (bx B + F_B(w.x),
+// by B + F_B(w.y)) with w the SEED draw (b, sweep); the bit of its cluster's
+// global root is set in `sel`.  Runs between the merge and the flip.  One
+// warp per seed: the seed's tile root is an edge root (its cluster may leave
+// the tile) iff it appears in the tile's seam record; then its global root is
+// found on gpar, otherwise the tile root is the cluster's root.
+__device__ __forceinline__ void few_select_seed(const SwRep& R, int ell, int64_t b, uint64_t sweep, uint32_t* sel,
+                                                int limit) {
+  const int lane = threadIdx.x & 31;
+  const Grid& g = R.g;
+  const int L = g.W;
+  const int B = L / ell;
+  const int by = (int)(b / ell), bx = (int)(b - (int64_t)by * ell);
+  const uint4 w = philox(make_uint4((uint32_t)b, (uint32_t)sweep, (uint32_t)(sweep >> 32), TAG_SEED),
+                         (uint32_t)R.seed, (uint32_t)(R.seed >> 32));
+  const int x = bx * B + state_of(w.x, B), y = by * B + state_of(w.y, B);
+  const int ty = y / TILE_H, tx = x / TILE_W;
+  const int t = ty * g.tiles_x + tx;
+  const int y0 = ty * TILE_H, x0 = tx * TILE_W;
+  const int r = R.lroot[(int64_t)y * L + x];
+  const int G = tile_global(r, y0, x0, L);
+  const int32_t* rec = R.s.seams + (int64_t)t * SeamLayout::INTS;
+  bool edge = false;
+  for (int k = lane; k < TILE_H; k += 32) edge |= rec[SeamLayout::COL_L + k] == G || rec[SeamLayout::COL_R + k] == G;
+  for (int k = lane; k < TILE_W; k += 32) edge |= rec[SeamLayout::ROW_B + k] == G || rec[SeamLayout::ROW_T + k] == G;
+  edge = __any_sync(FULL, edge);
+  if (lane == 0) {
+    const int root = edge ? g_find(R.gpar, G, limit, R.s.err) : G;
+    atomicOr(sel + (root >> 5), 1u << (root & 31));
+  }
 }
 
 }  // namespace swccl

@@ -23,6 +23,11 @@
 //
 // HBM traffic per site: spins read 1 B, 16-bit roots written and read 4 B,
 // spins written 1 B, plus seam records and edge-root entries.
+//
+// The few-cluster update (Sec. IV, variant (c)) shares k_sw_label and
+// k_merge; between the merge and the flip, k_few_select marks the global
+// roots of the clusters holding the ell^2 seeds in a bit array, and
+// k_sw_flip_few moves only those clusters (each with probability p_flip).
 #include "fused_tile.cuh"
 
 namespace swccl {
@@ -40,6 +45,21 @@ __global__ void __launch_bounds__(LABEL_THREADS, 5)
 k_sw_flip(SwRep R, const SwCtl* __restrict__ ctl, int limit) {
   __shared__ FlipTileSmem fs;
   sw_flip_tile(R, blockIdx.x, ctl->sweep, limit, fs);
+}
+
+__global__ void __launch_bounds__(LABEL_THREADS, 5)
+k_sw_flip_few(SwRep R, const SwCtl* __restrict__ ctl, int limit, const uint32_t* __restrict__ sel, uint64_t P) {
+  __shared__ FlipTileSmem fs;
+  sw_flip_tile<true>(R, blockIdx.x, ctl->sweep, limit, fs, sel, P);
+}
+
+constexpr int SELECT_THREADS = 256;
+
+__global__ void __launch_bounds__(SELECT_THREADS)
+k_few_select(SwRep R, const SwCtl* __restrict__ ctl, int ell, uint32_t* sel, int limit) {
+  const int64_t b = blockIdx.x * (int64_t)(SELECT_THREADS / 32) + (threadIdx.x >> 5);
+  if (b >= (int64_t)ell * ell) return;   // whole warps leave together
+  few_select_seed(R, ell, b, ctl->sweep, sel, limit);
 }
 
 // ---------------------------------------------------------------------------
@@ -134,6 +154,27 @@ cudaError_t launch_observe(const int8_t* spins, int L, int q, SwCtl* ctl, int64_
                            cudaStream_t st) {
   dim3 grid((unsigned)((L / 4 + OBS_THREADS - 1) / OBS_THREADS), (unsigned)((L + OBS_ROWS - 1) / OBS_ROWS));
   k_observe<<<grid, OBS_THREADS, 0, st>>>(spins, L, q, ctl, obs, obs_cap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_few_select(const uint16_t* lroot, int32_t* gpar, const Grid& g, const LabelScratch& s,
+                              uint64_t seed, int ell, uint32_t* sel, const SwCtl* ctl, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(sel, 0, few_sel_bytes(g.n_sites()), st);
+  if (e != cudaSuccess) return e;
+  const int limit = (int)std::min<int64_t>(g.n_sites() + 64, (int64_t)1 << 30);
+  const SwRep R = make_rep(nullptr, const_cast<uint16_t*>(lroot), gpar, nullptr, g, s, 2, 0, seed);
+  const int64_t seeds = (int64_t)ell * ell;
+  const int64_t blocks = (seeds + SELECT_THREADS / 32 - 1) / (SELECT_THREADS / 32);
+  k_few_select<<<(unsigned)blocks, SELECT_THREADS, 0, st>>>(R, ctl, ell, sel, limit);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sw_flip_few(int8_t* spins, const uint16_t* lroot, int32_t* gpar, const Grid& g,
+                               const LabelScratch& s, int q, uint64_t seed, const uint32_t* sel, uint64_t P,
+                               const SwCtl* ctl, cudaStream_t st) {
+  const int limit = (int)std::min<int64_t>(g.n_sites() + 64, (int64_t)1 << 30);
+  const SwRep R = make_rep(spins, const_cast<uint16_t*>(lroot), gpar, nullptr, g, s, q, 0, seed);
+  k_sw_flip_few<<<g.n_tiles(), LABEL_THREADS, 0, st>>>(R, ctl, limit, sel, P);
   return cudaGetLastError();
 }
 

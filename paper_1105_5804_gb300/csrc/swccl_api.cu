@@ -86,6 +86,10 @@ struct sw_handle {
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph_fused = nullptr;  // one fused sweep
   cudaGraphExec_t exec_fused = nullptr;
+  int update = SW_UPDATE_SW;         // SW_UPDATE_SW or SW_UPDATE_FEW (fused mode only)
+  int ell = 0;                       // few-cluster: ell x ell seed blocks
+  uint64_t P_flip = 0;               // few-cluster: flip threshold
+  uint32_t* sel = nullptr;           // few-cluster: seeded-cluster roots, one bit per site
   bool timing = false;
   bool dump_valid = false;  // mask/labels hold the last sweep's result
   std::vector<cudaEvent_t> ev_pending;   // SW_N_PHASES + 1 events per timed sweep
@@ -104,6 +108,7 @@ void free_handle(sw_handle* h) {
   for (auto e : h->ev_pending) cudaEventDestroy(e);
   for (auto e : h->ev_free) cudaEventDestroy(e);
   cudaFree(h->spins);
+  cudaFree(h->sel);
   cudaFree(h->mask);
   cudaFree(h->labels);
   cudaFree(h->scratch);
@@ -146,9 +151,18 @@ cudaError_t enqueue_sweep_fused(sw_handle* h, cudaEvent_t* ev) {
     return e;
   if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
   if ((e = launch_merge(h->labels, h->grid, h->ls, st))) return e;
-  if (ev && ((e = cudaEventRecord(ev[3], st)) != cudaSuccess || (e = cudaEventRecord(ev[4], st)) != cudaSuccess))
+  if (ev && (e = cudaEventRecord(ev[3], st)) != cudaSuccess) return e;
+  if (h->update == SW_UPDATE_FEW &&
+      (e = launch_few_select(h->lroot, h->labels, h->grid, h->ls, h->seed, h->ell, h->sel, h->ctl, st)))
     return e;
-  if ((e = launch_sw_flip(h->spins, h->lroot, h->labels, h->grid, h->ls, h->q, h->seed, h->ctl, st))) return e;
+  if (ev && (e = cudaEventRecord(ev[4], st)) != cudaSuccess) return e;
+  if (h->update == SW_UPDATE_FEW) {
+    if ((e = launch_sw_flip_few(h->spins, h->lroot, h->labels, h->grid, h->ls, h->q, h->seed, h->sel, h->P_flip,
+                                h->ctl, st)))
+      return e;
+  } else if ((e = launch_sw_flip(h->spins, h->lroot, h->labels, h->grid, h->ls, h->q, h->seed, h->ctl, st))) {
+    return e;
+  }
   if (ev && (e = cudaEventRecord(ev[5], st)) != cudaSuccess) return e;
   return launch_advance_fused(h->ctl, h->obs, OBS_CAP, h->q, st);
 }
@@ -196,6 +210,43 @@ const char* sw_last_error(void) { return g_err.c_str(); }
 
 uint64_t sw_threshold_for(int q, double beta, double J, int convention) {
   return threshold_of(coupling_K(q, beta, J, convention));
+}
+
+uint64_t sw_prob_threshold(double p) {
+  if (!(p >= 0.0 && p <= 1.0)) return UINT64_MAX;
+  const double t = std::floor(p * 4294967296.0);
+  return t >= 4294967296.0 ? (uint64_t)1 << 32 : (uint64_t)t;
+}
+
+int sw_set_update(sw_handle* h, int update, int ell, uint64_t P) {
+  if (!h || (update != SW_UPDATE_SW && update != SW_UPDATE_FEW)) return fail(SW_ERR_ARG, "sw_set_update: bad arguments");
+  if (update == SW_UPDATE_FEW) {
+    if (ell < 1 || h->L % ell != 0 || P > ((uint64_t)1 << 32))
+      return fail(SW_ERR_ARG, "sw_set_update: need ell >= 1 dividing L and P <= 2^32");
+    if (h->mode != SW_MODE_FUSED)
+      return fail(SW_ERR_STATE, "sw_set_update: the few-cluster update runs in SW_MODE_FUSED only");
+  } else {
+    ell = 0;
+    P = 0;
+  }
+  if (update == h->update && ell == h->ell && P == h->P_flip) return SW_OK;
+  CK(cudaStreamSynchronize(h->stream));
+  if (update == SW_UPDATE_FEW && !h->sel) {
+    if (cudaMalloc(&h->sel, (size_t)few_sel_bytes(h->grid.n_sites())) != cudaSuccess) {
+      cudaGetLastError();
+      h->sel = nullptr;
+      return fail(SW_ERR_OOM, "sw_set_update: cudaMalloc of the selection bits failed");
+    }
+  }
+  // ell and P are launch arguments of the captured sweep: capture it again
+  if (h->exec_fused) cudaGraphExecDestroy(h->exec_fused);
+  if (h->graph_fused) cudaGraphDestroy(h->graph_fused);
+  h->exec_fused = nullptr;
+  h->graph_fused = nullptr;
+  h->update = update;
+  h->ell = ell;
+  h->P_flip = P;
+  return SW_OK;
 }
 
 sw_handle* sw_create_threshold(int L, int q, uint64_t T, uint64_t seed, int hot_start, void* stream) {
@@ -320,6 +371,8 @@ int sw_sweep(sw_handle* h, int n) {
 int sw_set_mode(sw_handle* h, int mode) {
   if (!h || (mode != SW_MODE_STAGED && mode != SW_MODE_FUSED)) return fail(SW_ERR_ARG, "sw_set_mode: bad arguments");
   if (mode == h->mode) return SW_OK;
+  if (mode == SW_MODE_STAGED && h->update == SW_UPDATE_FEW)
+    return fail(SW_ERR_STATE, "sw_set_mode: the few-cluster update runs in SW_MODE_FUSED only");
   if (mode == SW_MODE_STAGED) {
     CK(finish_observables(h));
   } else {

@@ -11,7 +11,7 @@
 namespace swccl {
 
 // Philox tags (counter word 3).
-enum : uint32_t { TAG_BOND = 0, TAG_FLIP = 1, TAG_INIT = 2, TAG_PERC = 3 };
+enum : uint32_t { TAG_BOND = 0, TAG_FLIP = 1, TAG_INIT = 2, TAG_PERC = 3, TAG_SEED = 4 };
 
 // Tile of the local labeling phase: TILE_H rows x TILE_W columns, one CTA
 // per tile with one warp per 32-column strip (LABEL_THREADS = TILE_W).
@@ -163,6 +163,15 @@ cudaError_t launch_sw_flip(int8_t* spins, const uint16_t* lroot, int32_t* gpar, 
 cudaError_t launch_observe(const int8_t* spins, int L, int q, SwCtl* ctl, int64_t* obs, int obs_cap,
                            cudaStream_t st);
 cudaError_t launch_advance_fused(SwCtl* ctl, int64_t* obs, int obs_cap, int q, cudaStream_t st);
+// Few-cluster update: bytes of the seed-selection bit array of n sites, the
+// selection (clears the array, then marks the seeded clusters' roots), and
+// the flip of the selected clusters.
+inline int64_t few_sel_bytes(int64_t n_sites) { return (n_sites + 31) / 32 * 4; }
+cudaError_t launch_few_select(const uint16_t* lroot, int32_t* gpar, const Grid& g, const LabelScratch& s,
+                              uint64_t seed, int ell, uint32_t* sel, const SwCtl* ctl, cudaStream_t st);
+cudaError_t launch_sw_flip_few(int8_t* spins, const uint16_t* lroot, int32_t* gpar, const Grid& g,
+                               const LabelScratch& s, int q, uint64_t seed, const uint32_t* sel, uint64_t P,
+                               const SwCtl* ctl, cudaStream_t st);
 
 // Batched chains (k_batch.cu).
 cudaError_t launch_batch_label(const BatchView& b, BatchCtl* ctl, cudaStream_t st);
