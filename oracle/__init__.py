@@ -20,7 +20,7 @@ import numpy as np
 
 from . import build as _build
 
-TAG_BOND, TAG_FLIP, TAG_INIT, TAG_PERC, TAG_SEED = 0, 1, 2, 3, 4
+TAG_BOND, TAG_FLIP, TAG_INIT, TAG_PERC, TAG_SEED, TAG_BOND3 = 0, 1, 2, 3, 4, 5
 CONV_AUTO, CONV_POTTS, CONV_ISING = 0, 1, 2
 
 _lib = None
@@ -74,6 +74,22 @@ def lib():
                                    ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64, ctypes.c_void_p,
                                    ctypes.c_void_p]
         L.or_few_chain.restype = ctypes.c_int
+        i3 = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.or3_init_spins.argtypes = i3 + [ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p]
+        L.or3_init_spins.restype = None
+        L.or3_activate.argtypes = i3 + [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                        ctypes.c_void_p]
+        L.or3_activate.restype = None
+        L.or3_label.argtypes = i3 + [ctypes.c_void_p, ctypes.c_void_p]
+        L.or3_label.restype = ctypes.c_int64
+        L.or3_observables.argtypes = i3 + [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+        L.or3_observables.restype = None
+        L.or3_sweep.argtypes = i3 + [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        L.or3_sweep.restype = ctypes.c_int
+        L.or3_chain.argtypes = i3 + [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                     ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+        L.or3_chain.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -224,6 +240,60 @@ def few_chain(L: int, q: int, T: int, P: int, ell: int, seed: int, sweep0: int, 
     rc = lib().or_few_chain(L, q, T, P, ell, seed, sweep0, n_sweeps, _ptr(s), _ptr(obs))
     if rc != 0:
         raise ValueError("oracle few-cluster chain failed (ell must divide L)")
+    return s, obs
+
+
+# --------------------------------------------------------------------------
+# Simple-cubic lattice X x Y x Z (periodic), site i = (z*Y + y)*X + x; bond
+# mask one byte per site, bit d = bond to the +x / +y / +z neighbour
+# --------------------------------------------------------------------------
+def init_spins3(X: int, Y: int, Z: int, q: int, seed: int, hot: bool) -> np.ndarray:
+    s = np.empty(X * Y * Z, dtype=np.int8)
+    lib().or3_init_spins(X, Y, Z, q, seed, int(bool(hot)), _ptr(s))
+    return s
+
+
+def activate3(X: int, Y: int, Z: int, spins, seed: int, sweep_index: int, T: int) -> np.ndarray:
+    spins = _c(spins, np.int8).reshape(-1)
+    m = np.zeros(X * Y * Z, dtype=np.uint8)
+    lib().or3_activate(X, Y, Z, _ptr(spins), seed, sweep_index, T, _ptr(m))
+    return m
+
+
+def label3(mask, X: int, Y: int, Z: int):
+    """Canonical labels of a 3D bond mask.  Returns (labels, number of clusters)."""
+    mask = _c(mask, np.uint8).reshape(-1)
+    lab = np.empty(X * Y * Z, dtype=np.int32)
+    n = lib().or3_label(X, Y, Z, _ptr(mask), _ptr(lab))
+    if n < 0:
+        raise MemoryError("oracle 3D labeling failed")
+    return lab, int(n)
+
+
+def observables3(X: int, Y: int, Z: int, q: int, spins) -> np.ndarray:
+    spins = _c(spins, np.int8).reshape(-1)
+    out = np.zeros(1 + q, dtype=np.int64)
+    lib().or3_observables(X, Y, Z, q, _ptr(spins), _ptr(out))
+    return out
+
+
+def sweep3(X: int, Y: int, Z: int, q: int, T: int, seed: int, sweep_index: int, spins):
+    """One 3D sweep.  Returns (new spins, mask, canonical labels, observables)."""
+    s = _c(spins, np.int8).reshape(-1).copy()
+    m = np.zeros(X * Y * Z, dtype=np.uint8)
+    lab = np.empty(X * Y * Z, dtype=np.int32)
+    obs = np.zeros(1 + q, dtype=np.int64)
+    if lib().or3_sweep(X, Y, Z, q, T, seed, sweep_index, _ptr(s), _ptr(m), _ptr(lab), _ptr(obs)) != 0:
+        raise MemoryError("oracle 3D sweep failed")
+    return s, m, lab, obs
+
+
+def chain3(X: int, Y: int, Z: int, q: int, T: int, seed: int, sweep0: int, n_sweeps: int, spins):
+    """n_sweeps 3D sweeps from sweep0.  Returns (final spins, obs)."""
+    s = _c(spins, np.int8).reshape(-1).copy()
+    obs = np.zeros((n_sweeps, 1 + q), dtype=np.int64)
+    if lib().or3_chain(X, Y, Z, q, T, seed, sweep0, n_sweeps, _ptr(s), _ptr(obs)) != 0:
+        raise MemoryError("oracle 3D chain failed")
     return s, obs
 
 

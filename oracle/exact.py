@@ -62,6 +62,40 @@ def enumerate_potts(Lx, Ly, q):
     return n_eq, counts
 
 
+def _cubic_bonds(X, Y, Z):
+    """List of (i, j) for the 3N bonds of a periodic X x Y x Z box, site
+    i = (z Y + y) X + x, each site bonded to its +x, +y, +z neighbour (for a
+    side of 2 the two bonds between a pair are distinct bonds)."""
+    bonds = []
+    for z in range(Z):
+        for y in range(Y):
+            for x in range(X):
+                i = (z * Y + y) * X + x
+                bonds.append((i, (z * Y + y) * X + (x + 1) % X))
+                bonds.append((i, (z * Y + (y + 1) % Y) * X + x))
+                bonds.append((i, (((z + 1) % Z) * Y + y) * X + x))
+    return bonds
+
+
+def enumerate_potts_3d(X, Y, Z, q):
+    """All q^N states of the periodic X x Y x Z simple-cubic box; same
+    returns as enumerate_potts."""
+    N = X * Y * Z
+    n_states = q ** N
+    if n_states > (1 << 22):
+        raise ValueError("too many states for brute force")
+    idx = np.arange(n_states, dtype=np.int64)
+    spins = np.empty((n_states, N), dtype=np.int8)
+    for site in range(N):
+        spins[:, site] = idx % q
+        idx //= q
+    n_eq = np.zeros(n_states, dtype=np.int64)
+    for i, j in _cubic_bonds(X, Y, Z):
+        n_eq += spins[:, i] == spins[:, j]
+    counts = np.stack([(spins == k).sum(axis=1) for k in range(q)], axis=1).astype(np.int64)
+    return n_eq, counts
+
+
 def moments_from_states(n_eq, counts, K, q):
     """Exact Boltzmann averages at coupling K (Potts delta convention):
     <n_eq>, <n_eq^2>, and for q = 2 <|M|>, <M^2> with M = n_0 - n_1."""

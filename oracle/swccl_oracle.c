@@ -33,6 +33,8 @@
  *       tag 2 INIT: c0 = i, word 0, sweep 0
  *       tag 3 PERC: key = (k, 0), sweep 0, word mapping as BOND
  *       tag 4 SEED: c0 = seed block index (few-cluster update), words 0, 1
+ *       tag 5 BOND3: simple-cubic lattice, c0 = i, word = dir
+ *                    (0 = +x, 1 = +y, 2 = +z)
  *   - a bond between equal spins is open iff (uint64)r < T,
  *     T = min(2^32, floor(p * 2^32))
  *   - new cluster state F_q(w) = floor(w * q / 2^32)
@@ -54,7 +56,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-enum { OR_TAG_BOND = 0, OR_TAG_FLIP = 1, OR_TAG_INIT = 2, OR_TAG_PERC = 3, OR_TAG_SEED = 4 };
+enum { OR_TAG_BOND = 0, OR_TAG_FLIP = 1, OR_TAG_INIT = 2, OR_TAG_PERC = 3, OR_TAG_SEED = 4, OR_TAG_BOND3 = 5 };
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10, written from the SC'11 description.                        */
@@ -370,6 +372,126 @@ int or_few_chain(int L, int q, uint64_t T, uint64_t P, int ell, uint64_t seed, u
     for (int64_t s = 0; s < n_sweeps && rc == 0; s++)
         rc = or_few_sweep(L, q, T, P, ell, seed, sweep0 + (uint64_t)s, spins, mask, labels,
                           obs ? obs + s * (1 + q) : NULL);
+    free(mask);
+    free(labels);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Simple-cubic lattice (the generalisation the paper names in Secs. II and  */
+/* II.B: the same three SW steps with six neighbours instead of four).       */
+/* Box X x Y x Z, periodic; site i = (z*Y + y)*X + x; each site owns its      */
+/* bonds to (x+1, y, z), (x, y+1, z), (x, y, z+1).  Bond mask: one byte per   */
+/* site, bit d = bond in direction d (0 = +x, 1 = +y, 2 = +z).                */
+/* ------------------------------------------------------------------------ */
+static int64_t nb3(int X, int Y, int Z, int64_t i, int dir)
+{
+    int64_t x = i % X, y = (i / X) % Y, z = i / ((int64_t)X * Y);
+    if (dir == 0) x = (x + 1) % X;
+    else if (dir == 1) y = (y + 1) % Y;
+    else z = (z + 1) % Z;
+    return (z * Y + y) * X + x;
+}
+
+void or3_init_spins(int X, int Y, int Z, int q, uint64_t seed, int hot, int8_t* spins)
+{
+    int64_t N = (int64_t)X * Y * Z;
+    for (int64_t i = 0; i < N; i++)
+        spins[i] = hot ? (int8_t)or_flip_state(draw_word(seed, (uint32_t)i, 0, OR_TAG_INIT, 0), q) : 0;
+}
+
+/* Eq. 7 on the three bonds each site owns. */
+void or3_activate(int X, int Y, int Z, const int8_t* spins, uint64_t seed, uint64_t sweep, uint64_t T,
+                  uint8_t* mask)
+{
+    int64_t N = (int64_t)X * Y * Z;
+    for (int64_t i = 0; i < N; i++) {
+        mask[i] = 0;
+        for (int dir = 0; dir < 3; dir++) {
+            if (spins[i] != spins[nb3(X, Y, Z, i, dir)]) continue;
+            uint32_t r = draw_word(seed, (uint32_t)i, sweep, OR_TAG_BOND3, dir);
+            if ((uint64_t)r < T) mask[i] |= (uint8_t)(1u << dir);
+        }
+    }
+}
+
+/* Breadth-first search seeded in site order (Sec. II.B.1), six neighbours:
+ * labels = smallest site index of the cluster.  Returns the number of
+ * clusters, or -1 on allocation failure. */
+int64_t or3_label(int X, int Y, int Z, const uint8_t* mask, int32_t* labels)
+{
+    int64_t N = (int64_t)X * Y * Z;
+    int64_t* queue = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+    if (!queue) return -1;
+    for (int64_t i = 0; i < N; i++) labels[i] = -1;
+    int64_t n_clusters = 0;
+    for (int64_t seed = 0; seed < N; seed++) {
+        if (labels[seed] != -1) continue;
+        n_clusters++;
+        labels[seed] = (int32_t)seed;
+        int64_t head = 0, tail = 0;
+        queue[tail++] = seed;
+        while (head < tail) {
+            int64_t u = queue[head++];
+            int64_t x = u % X, y = (u / X) % Y, z = u / ((int64_t)X * Y);
+            for (int dir = 0; dir < 3; dir++) {
+                /* forward: u's own bond; backward: the bond the neighbour
+                 * below in this direction owns */
+                int64_t fwd = nb3(X, Y, Z, u, dir);
+                int64_t bx = x, by = y, bz = z;
+                if (dir == 0) bx = (x + X - 1) % X;
+                else if (dir == 1) by = (y + Y - 1) % Y;
+                else bz = (z + Z - 1) % Z;
+                int64_t bwd = (bz * Y + by) * X + bx;
+                if (((mask[u] >> dir) & 1) && labels[fwd] == -1) {
+                    labels[fwd] = (int32_t)seed;
+                    queue[tail++] = fwd;
+                }
+                if (((mask[bwd] >> dir) & 1) && labels[bwd] == -1) {
+                    labels[bwd] = (int32_t)seed;
+                    queue[tail++] = bwd;
+                }
+            }
+        }
+    }
+    free(queue);
+    return n_clusters;
+}
+
+/* n_eq over the 3N bonds, then sites per state. */
+void or3_observables(int X, int Y, int Z, int q, const int8_t* spins, int64_t* out)
+{
+    int64_t N = (int64_t)X * Y * Z;
+    for (int k = 0; k <= q; k++) out[k] = 0;
+    for (int64_t i = 0; i < N; i++) {
+        for (int dir = 0; dir < 3; dir++)
+            if (spins[i] == spins[nb3(X, Y, Z, i, dir)]) out[0]++;
+        out[1 + spins[i]]++;
+    }
+}
+
+int or3_sweep(int X, int Y, int Z, int q, uint64_t T, uint64_t seed, uint64_t sweep, int8_t* spins,
+              uint8_t* mask, int32_t* labels, int64_t* obs)
+{
+    int64_t N = (int64_t)X * Y * Z;
+    or3_activate(X, Y, Z, spins, seed, sweep, T, mask);
+    if (or3_label(X, Y, Z, mask, labels) < 0) return -1;
+    or_flip(N, q, seed, sweep, labels, spins);
+    if (obs) or3_observables(X, Y, Z, q, spins, obs);
+    return 0;
+}
+
+int or3_chain(int X, int Y, int Z, int q, uint64_t T, uint64_t seed, uint64_t sweep0, int64_t n_sweeps,
+              int8_t* spins, int64_t* obs)
+{
+    int64_t N = (int64_t)X * Y * Z;
+    uint8_t* mask = (uint8_t*)malloc((size_t)N);
+    int32_t* labels = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);
+    if (!mask || !labels) { free(mask); free(labels); return -1; }
+    int rc = 0;
+    for (int64_t s = 0; s < n_sweeps && rc == 0; s++)
+        rc = or3_sweep(X, Y, Z, q, T, seed, sweep0 + (uint64_t)s, spins, mask, labels,
+                       obs ? obs + s * (1 + q) : NULL);
     free(mask);
     free(labels);
     return rc;
