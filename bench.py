@@ -291,6 +291,38 @@ def few_cluster_secondary(torch, sw, L=L_BENCH, ells=(16, 256), p_flip=0.5, warm
             "warmup_sweeps": warm, "sweeps": sweeps, "rows": out}
 
 
+KC3_ISING = 0.2216546   # simple-cubic Ising critical coupling (literature value)
+
+
+def cubic_secondary(torch, sw, L=512, warm=20, sweeps=50):
+    """Simple-cubic lattice (the paper's 3D generalisation): q = 2 at the
+    critical coupling, L^3 sites, hot start seed 7; whole sweeps timed with
+    events on the handle's stream, then one timed-mode pass for the split."""
+    h = sw.sw3_create_ex(L, L, L, 2, KC3_ISING, 1.0, sw.SW_CONV_ISING, SEED_BENCH, True)
+    try:
+        sw.sw3_sweep(h, warm)
+        st = torch.cuda.ExternalStream(sw.sw3_stream(h))
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        sw.sw3_sweep(h, sweeps)
+        b.record(st)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        obs = sw.sw3_observables(h, 4096)
+        sw.sw3_set_timing(h, True)
+        sw.sw3_sweep(h, 10)
+        phases, n = sw.sw3_phase_times(h)
+    finally:
+        sw.sw3_destroy(h)
+    N = L ** 3
+    return {"workload": "sw3_ising_q2_L%d_cubed_Kc_hot_start_seed7" % L, "value": N * sweeps / (ms * 1e6),
+            "unit": "site-updates/ns", "ms_per_sweep": ms / sweeps, "sweeps": sweeps, "warmup_sweeps": warm,
+            "mean_n_eq_per_site": float(obs[-sweeps:, 0].mean()) / N,
+            "phase_ms_per_sweep": {k: v / n for k, v in phases.items()}}
+
+
 def philox_ceiling(torch, sw, reps=3):
     """Measured integer-ALU ceiling: Philox4x32-10 calls per second of a
     kernel that does nothing else, 8 CTAs x 256 threads per SM on every SM."""
@@ -475,6 +507,7 @@ def run_ours(args):
         sw.sw_destroy(h4)
         secondary["table_L8192"] = table_secondary(torch, sw)
         secondary["few_cluster"] = few_cluster_secondary(torch, sw)
+        secondary["cubic"] = cubic_secondary(torch, sw)
         secondary["batch_512"] = batch_secondary(torch, sw)
         secondary["serving"] = serving_secondary(torch)
     sw.sw_destroy(h)

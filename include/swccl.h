@@ -218,6 +218,63 @@ int sw_set_update(sw_handle* h, int update, int ell, uint64_t P);
 uint64_t sw_prob_threshold(double p);
 
 /* ------------------------------------------------------------------------ */
+/* Simple-cubic lattice (the paper's three-dimensional generalisation,      */
+/* Secs. II and II.B: the same three steps with six neighbours)             */
+/* ------------------------------------------------------------------------ */
+
+/* A chain on the periodic X x Y x Z simple-cubic lattice: int8 spins, site
+ * i = (z*Y + y)*X + x.  Each site owns its bonds to (x+1, y, z), (x, y+1, z)
+ * and (x, y, z+1); bond d of site i is open iff the spins are equal and word
+ * d of the Philox draw with counter (i, sweep_lo, sweep_hi, 5) is below T
+ * (Eq. 7; no draw when T is 0 or 2^32).  Clusters, canonical labels (the
+ * cluster's minimum site index), the flip (FLIP draw keyed by the root,
+ * F_q of word 0) and the observables (n_eq over the 3N bonds, then n_k) are
+ * as on the square lattice.  Hot start: INIT draw of site i as in 2D.
+ * Requires X, Y, Z >= 1 with X*Y*Z <= 2^30, 2 <= q <= 127, T <= 2^32.  The
+ * library owns the device memory: 5 bytes per site plus the observable
+ * ring.  NULL on failure (see sw_last_error).  Each sweep is four kernels
+ * (brick-local union-find, face merge, flip, observables), replayed as a
+ * captured CUDA graph unless timing is on. */
+typedef struct sw3_handle sw3_handle;
+#define SW3_N_PHASES 4   /* local, merge, flip, observables */
+
+sw3_handle* sw3_create(int X, int Y, int Z, int q, uint64_t T, uint64_t seed, int hot_start, void* stream);
+sw3_handle* sw3_create_ex(int X, int Y, int Z, int q, double beta, double J, int convention, uint64_t seed,
+                          int hot_start, void* stream);
+int sw3_destroy(sw3_handle* h);
+
+/* n sweeps, asynchronously on the handle's stream. */
+int sw3_sweep(sw3_handle* h, int n);
+
+/* Waits for the stream; reports device-side failures (SW_ERR_STATE). */
+int sw3_sync(sw3_handle* h);
+
+/* Per-sweep (n_eq, n_0 .. n_{q-1}) not yet read, oldest first, at most
+ * max_sweeps rows of 1 + q int64 (the ring keeps the last 4096).
+ * Synchronises. */
+int sw3_observables(sw3_handle* h, int64_t* out, int max_sweeps, int* n_written);
+
+/* Copy the spins (int8[X*Y*Z]) out / in, host (is_device == 0) or device
+ * memory; set_spins rejects values outside [0, q) with SW_ERR_ARG and keeps
+ * the old spins.  Synchronise. */
+int sw3_get_spins(sw3_handle* h, int8_t* dst, int is_device);
+int sw3_set_spins(sw3_handle* h, const int8_t* src, int is_device);
+
+/* Canonical labels (int32[X*Y*Z]) of the clusters of the last sweep, for
+ * bit-exact checks.  SW_ERR_STATE before the first sweep and after a host
+ * sw3_set_spins.  Synchronises. */
+int sw3_labels(sw3_handle* h, int32_t* out, int is_device);
+
+void* sw3_stream(sw3_handle* h);
+
+/* info[0..7] = X, Y, Z, q, T, seed, sweeps enqueued, observable ring size. */
+int sw3_get_info(sw3_handle* h, int64_t* info);
+
+/* Per-phase timing as sw_set_timing / sw_phase_times, SW3_N_PHASES phases. */
+int sw3_set_timing(sw3_handle* h, int enable);
+int sw3_phase_times(sw3_handle* h, double* ms, int64_t* n_sweeps);
+
+/* ------------------------------------------------------------------------ */
 /* Batches of independent chains (no counterpart in the paper: many         */
 /* replicas of uneven size and temperature advanced together)               */
 /* ------------------------------------------------------------------------ */

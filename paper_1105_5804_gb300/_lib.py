@@ -20,6 +20,8 @@ SW_MODE_STAGED, SW_MODE_FUSED = 0, 1
 SW_BATCH_PHASES, SW_BATCH_PERSISTENT = 0, 1
 SW_UPDATE_SW, SW_UPDATE_FEW = 0, 1
 PHASE_NAMES = ("activate", "local", "merge", "roots", "flip")
+SW3_N_PHASES = 4
+PHASE_NAMES3 = ("local", "merge", "flip", "observe")
 
 
 class SwcclError(RuntimeError):
@@ -80,6 +82,19 @@ def lib():
         "sw_batch_get_spins": ([vp, i32, vp, i32], i32),
         "sw_batch_info": ([vp, vp], i32),
         "sw_batch_stream": ([vp], vp),
+        "sw3_create": ([i32, i32, i32, i32, u64, u64, i32, vp], vp),
+        "sw3_create_ex": ([i32, i32, i32, i32, dbl, dbl, i32, u64, i32, vp], vp),
+        "sw3_destroy": ([vp], i32),
+        "sw3_sweep": ([vp, i32], i32),
+        "sw3_sync": ([vp], i32),
+        "sw3_observables": ([vp, vp, i32, ctypes.POINTER(i32)], i32),
+        "sw3_get_spins": ([vp, vp, i32], i32),
+        "sw3_set_spins": ([vp, vp, i32], i32),
+        "sw3_labels": ([vp, vp, i32], i32),
+        "sw3_stream": ([vp], vp),
+        "sw3_get_info": ([vp, vp], i32),
+        "sw3_set_timing": ([vp, i32], i32),
+        "sw3_phase_times": ([vp, vp, ctypes.POINTER(i64)], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -246,6 +261,104 @@ def sw_phase_times(h):
     n = ctypes.c_int64(0)
     _check(lib().sw_phase_times(h, ms.ctypes.data, ctypes.byref(n)))
     return dict(zip(PHASE_NAMES, ms.tolist())), int(n.value)
+
+
+# ---------------------------------------------------------------------------
+# Simple-cubic chains
+# ---------------------------------------------------------------------------
+def sw3_create(X, Y, Z, q, T, seed, hot_start=False, stream=0):
+    return _handle(lib().sw3_create(X, Y, Z, q, T, seed, 1 if hot_start else 0,
+                                    _stream(stream) if stream else None))
+
+
+def sw3_create_ex(X, Y, Z, q, beta, J=1.0, convention=SW_CONV_AUTO, seed=0, hot_start=False, stream=0):
+    return _handle(lib().sw3_create_ex(X, Y, Z, q, beta, J, convention, seed, 1 if hot_start else 0,
+                                       _stream(stream) if stream else None))
+
+
+def sw3_destroy(h):
+    _check(lib().sw3_destroy(h))
+
+
+def sw3_sweep(h, n):
+    _check(lib().sw3_sweep(h, n))
+
+
+def sw3_sync(h):
+    _check(lib().sw3_sync(h))
+
+
+def sw3_get_info(h):
+    info = np.zeros(8, dtype=np.int64)
+    _check(lib().sw3_get_info(h, info.ctypes.data))
+    keys = ("X", "Y", "Z", "q", "T", "seed", "sweeps", "obs_cap")
+    return {k: int(v) for k, v in zip(keys, info)}
+
+
+def _n3(h):
+    i = sw3_get_info(h)
+    return i["X"] * i["Y"] * i["Z"]
+
+
+def sw3_observables(h, max_sweeps=4096):
+    q = sw3_get_info(h)["q"]
+    out = np.zeros((max_sweeps, 1 + q), dtype=np.int64)
+    n = ctypes.c_int(0)
+    _check(lib().sw3_observables(h, out.ctypes.data, max_sweeps, ctypes.byref(n)))
+    return out[: n.value]
+
+
+def sw3_get_spins(h, out=None):
+    """Current spins into ``out`` (host int8 array or CUDA int8 tensor) or a new array."""
+    N = _n3(h)
+    if out is None or isinstance(out, np.ndarray):
+        a = np.empty(N, dtype=np.int8) if out is None else out
+        if a.dtype != np.int8 or a.size < N or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("out must be a contiguous int8 array of %d elements" % N)
+        _check(lib().sw3_get_spins(h, a.ctypes.data, 0))
+        return a
+    import torch
+    _check(lib().sw3_get_spins(h, _dev(out, torch.int8, N, "out"), 1))
+    return out
+
+
+def sw3_set_spins(h, src):
+    import torch
+    N = _n3(h)
+    if isinstance(src, torch.Tensor) and src.is_cuda:
+        _check(lib().sw3_set_spins(h, _dev(src, torch.int8, N, "src"), 1))
+    else:
+        a = np.ascontiguousarray(src, dtype=np.int8).reshape(-1)
+        if a.size != N:
+            raise ValueError("need %d spins" % N)
+        _check(lib().sw3_set_spins(h, a.ctypes.data, 0))
+
+
+def sw3_labels(h, out=None):
+    """Canonical labels of the last sweep's clusters (numpy, or into a CUDA int32 tensor)."""
+    N = _n3(h)
+    if out is None:
+        a = np.empty(N, dtype=np.int32)
+        _check(lib().sw3_labels(h, a.ctypes.data, 0))
+        return a
+    import torch
+    _check(lib().sw3_labels(h, _dev(out, torch.int32, N, "out"), 1))
+    return out
+
+
+def sw3_stream(h):
+    return lib().sw3_stream(h)
+
+
+def sw3_set_timing(h, enable):
+    _check(lib().sw3_set_timing(h, 1 if enable else 0))
+
+
+def sw3_phase_times(h):
+    ms = np.zeros(SW3_N_PHASES, dtype=np.float64)
+    n = ctypes.c_int64(0)
+    _check(lib().sw3_phase_times(h, ms.ctypes.data, ctypes.byref(n)))
+    return dict(zip(PHASE_NAMES3, ms.tolist())), int(n.value)
 
 
 # ---------------------------------------------------------------------------

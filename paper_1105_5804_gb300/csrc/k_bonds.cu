@@ -155,6 +155,13 @@ cudaError_t launch_init_spins(int8_t* spins, int L, int q, uint64_t seed, int ho
   return cudaGetLastError();
 }
 
+cudaError_t launch_init_spins_n(int8_t* spins, int64_t n, int q, uint64_t seed, int hot, cudaStream_t st) {
+  const int threads = 256;
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, 152 * 64));
+  k_init_spins<<<(unsigned)blocks, threads, 0, st>>>(spins, n, q, seed, hot);
+  return cudaGetLastError();
+}
+
 __global__ void k_check_spins(const int8_t* __restrict__ spins, int64_t n, int q, int* err) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {

@@ -11,7 +11,7 @@
 namespace swccl {
 
 // Philox tags (counter word 3).
-enum : uint32_t { TAG_BOND = 0, TAG_FLIP = 1, TAG_INIT = 2, TAG_PERC = 3, TAG_SEED = 4 };
+enum : uint32_t { TAG_BOND = 0, TAG_FLIP = 1, TAG_INIT = 2, TAG_PERC = 3, TAG_SEED = 4, TAG_BOND3 = 5 };
 
 // Tile of the local labeling phase: TILE_H rows x TILE_W columns, one CTA
 // per tile with one warp per 32-column strip (LABEL_THREADS = TILE_W).
@@ -41,6 +41,14 @@ struct Grid {
   int periodic;
   __host__ __device__ int64_t n_sites() const { return (int64_t)H * W; }
   __host__ __device__ int n_tiles() const { return tiles_x * tiles_y; }
+};
+
+// Periodic X x Y x Z simple-cubic box and its bricks (k_cubic.cu).
+struct Box3 {
+  int X, Y, Z;
+  int bx, by, bz;   // bricks per axis
+  __host__ __device__ int64_t n() const { return (int64_t)X * Y * Z; }
+  __host__ __device__ int64_t n_bricks() const { return (int64_t)bx * by * bz; }
 };
 
 inline Grid make_grid(int H, int W, int periodic) {
@@ -139,6 +147,13 @@ cudaError_t launch_pixel_bonds(const uint8_t* px, uint8_t* mask, int H, int W, i
                                cudaStream_t st);
 cudaError_t launch_philox_probe(long long calls_per_thread, int blocks, uint32_t* sink, cudaStream_t st);
 cudaError_t launch_check_spins(const int8_t* spins, int64_t n, int q, int* err, cudaStream_t st);
+cudaError_t launch_init_spins_n(int8_t* spins, int64_t n, int q, uint64_t seed, int hot, cudaStream_t st);
+// Simple-cubic sweep (k_cubic.cu).  ev, if not null, receives five events:
+// before the local step, merge, flip, observables, and after the advance.
+Box3 make_box3(int X, int Y, int Z);
+cudaError_t launch_sweep3(int8_t* spins, int32_t* gpar, const Box3& b, int q, uint64_t T, uint64_t seed, SwCtl* ctl,
+                          int64_t* obs, int obs_cap, cudaStream_t st, cudaEvent_t* ev);
+cudaError_t launch_labels3(int32_t* gpar, int32_t* out, const Box3& b, int* err, cudaStream_t st);
 
 cudaError_t launch_tile_label(const uint8_t* mask, int32_t* labels, const Grid& g,
                               const LabelScratch& s, cudaStream_t st);
