@@ -201,9 +201,9 @@ int sw_phase_times(sw_handle* h, double* ms, int64_t* n_sweeps);
  *     of the SW sweep with the same arguments.  P = p_flip 2^32 (see
  *     sw_prob_threshold); the paper asks p_flip < 1 for ergodicity, P = 2^32
  *     (always flip) is accepted too.
- * Cost: the SW sweep plus one warp per seed reading the seed tile's seam
- * record (2.3 KB) and a memset of L*L/8 bytes; meant for few seeds
- * (ell up to about L/32). */
+ * Cost: the SW sweep plus a memset of L*L/8 bytes and one thread per seed
+ * (two tile-root reads and, for a cluster that leaves its tile, one root
+ * lookup). */
 #define SW_UPDATE_SW 0
 #define SW_UPDATE_FEW 1
 

@@ -149,17 +149,30 @@ constexpr int QREG = QREG_MAX;   // state counts kept in registers for q <= QREG
 }  // namespace fused
 using namespace fused;
 
+// After the labeling kernel, the first TILE_SITES / 32 words of a tile's
+// pair-list slot (no longer needed once the tile is labeled) hold its
+// edge-root bits: bit r set iff local root r's component touches the tile
+// edge, so that its cluster may continue in other tiles.  The flip and the
+// few-cluster seed selection read them.
+constexpr int EDGE_WORDS = TILE_SITES / 32;
+static_assert(EDGE_WORDS == LABEL_THREADS, "one edge word per thread");
+// Flag on a root-list entry (local indices are below TILE_SITES).
+constexpr uint16_t EDGE_ROOT = 0x8000u;
+constexpr uint16_t ROOT_MASK = 0x7FFFu;
+static_assert(TILE_SITES <= ROOT_MASK + 1, "local index fits below the flag");
+
 struct LabelTileSmem {
   TileSmem tile;
+  uint32_t edge_bits[EDGE_WORDS];                   // local roots on the tile edge
   uint32_t e_last;                                  // raw east bit of column w-1, bit = row
   unsigned long long red[(1 + QREG) * (LABEL_THREADS / 32)];
   int hist[128];
 };
 
 struct FlipTileSmem {
-  uint16_t rlist[TILE_SITES];
-  uint8_t ns[TILE_SITES];
-  uint32_t edge_mark[TILE_SITES / 32];
+  uint16_t rlist[TILE_SITES];   // the tile's roots (EDGE_ROOT flag on edge roots)
+  uint8_t ns[TILE_SITES];       // new state, indexed by local root
+  uint32_t edge_bits[EDGE_WORDS];
   int warp_cnt[LABEL_THREADS / 32];
 };
 
@@ -190,6 +203,7 @@ __device__ __forceinline__ void sw_label_tile(const SwRep& R, int t, uint64_t sw
     e_last = 0u;
   }
   for (int k = threadIdx.x; k < 128; k += LABEL_THREADS) hist[k] = 0;
+  ls.edge_bits[threadIdx.x] = 0u;
   __syncthreads();
 
   // 1. bonds: warp c draws strip c, lane ly row ly
@@ -230,40 +244,57 @@ __device__ __forceinline__ void sw_label_tile(const SwRep& R, int t, uint64_t sw
   // 2. label the tile
   tile_engine(sm, h, w, slot, hook_log, s.err);
 
-  // 3. tile roots as 16-bit local indices, two sites per store
-  for (int k = threadIdx.x; k < TILE_SITES / 2; k += LABEL_THREADS) {
-    const int sidx = 2 * k;
+  // 3. tile roots as 16-bit local indices, eight sites per thread and store
+  auto entry = [&](int p) -> uint32_t { return (uint32_t)sm.par[p]; };   // p = par[site]
+  for (int k = threadIdx.x; k < TILE_SITES / 8; k += LABEL_THREADS) {
+    const int sidx = 8 * k;
     const int ly = sidx >> TILE_W_LOG2, lx = sidx & (TILE_W - 1);
-    if (ly < h && lx < w) {   // w is a multiple of 4: both sites are inside
-      const uint32_t r0 = (uint32_t)sm.par[sm.par[sidx]], r1 = (uint32_t)sm.par[sm.par[sidx + 1]];
-      *reinterpret_cast<uint32_t*>(lroot + (int64_t)(y0 + ly) * L + x0 + lx) = r0 | (r1 << 16);
+    if (ly >= h || lx >= w) continue;   // w is a multiple of 4: the first four sites are inside
+    const int4 pa = *reinterpret_cast<const int4*>(&sm.par[sidx]);
+    const uint2 lo = make_uint2(entry(pa.x) | (entry(pa.y) << 16),
+                                entry(pa.z) | (entry(pa.w) << 16));
+    uint16_t* dst = lroot + (int64_t)(y0 + ly) * L + x0 + lx;
+    if (lx + 8 <= w) {
+      const int4 pb = *reinterpret_cast<const int4*>(&sm.par[sidx + 4]);
+      const uint2 hi = make_uint2(entry(pb.x) | (entry(pb.y) << 16),
+                                  entry(pb.z) | (entry(pb.w) << 16));
+      if ((L & 7) == 0) {   // row starts 16-byte aligned
+        *reinterpret_cast<uint4*>(dst) = make_uint4(lo.x, lo.y, hi.x, hi.y);
+      } else {              // L % 4 == 0: 8-byte aligned
+        *reinterpret_cast<uint2*>(dst) = lo;
+        *reinterpret_cast<uint2*>(dst + 4) = hi;
+      }
+    } else {
+      *reinterpret_cast<uint2*>(dst) = lo;
     }
   }
 
-  // 4. seam record; parent entries of edge roots
+  // 4. seam record; parent entries of edge roots; edge roots marked
   int32_t* rec = s.seams + (int64_t)t * SeamLayout::INTS;
-  auto groot = [&](int ly, int lx) -> int32_t { return tile_global(sm.par[sm.par[ly * TILE_W + lx]], y0, x0, L); };
-  auto init_parent = [&](bool ok, int32_t r) {
-    // one write per run of equal roots among consecutive lanes
-    const int32_t left = __shfl_up_sync(FULL, r, 1);
-    if (ok && (lane == 0 || left != r)) gpar[r] = r;
+  uint32_t* edge_bits = ls.edge_bits;
+  auto root_at = [&](int ly, int lx) -> int { return sm.par[sm.par[ly * TILE_W + lx]]; };
+  auto edge_root = [&](bool ok, int r) -> int32_t {
+    // global index of local root r; the first of a run of equal roots among
+    // consecutive lanes writes its parent entry and its edge mark
+    const int left = __shfl_up_sync(FULL, ok ? r : -1, 1);
+    if (!ok) return -1;
+    const int32_t gr = tile_global(r, y0, x0, L);
+    if (lane == 0 || left != r) {
+      gpar[gr] = gr;
+      atomicOr(&edge_bits[r >> 5], 1u << (r & 31));
+    }
+    return gr;
   };
   for (int k = threadIdx.x; k < TILE_H; k += LABEL_THREADS) {
     const bool ok = k < h;
-    const int32_t a = ok ? groot(k, 0) : -1, b = ok ? groot(k, w - 1) : -1;
-    rec[SeamLayout::COL_L + k] = a;
-    rec[SeamLayout::COL_R + k] = b;
-    init_parent(ok, a);
-    init_parent(ok, b);
+    rec[SeamLayout::COL_L + k] = edge_root(ok, ok ? root_at(k, 0) : 0);
+    rec[SeamLayout::COL_R + k] = edge_root(ok, ok ? root_at(k, w - 1) : 0);
     if (lane == 0) rec[SeamLayout::E_BITS + (k >> 5)] = (int32_t)e_last;
   }
   for (int k = threadIdx.x; k < TILE_W; k += LABEL_THREADS) {
     const bool ok = k < w;
-    const int32_t a = ok ? groot(0, k) : -1, b = ok ? groot(h - 1, k) : -1;
-    rec[SeamLayout::ROW_B + k] = a;
-    rec[SeamLayout::ROW_T + k] = b;
-    init_parent(ok, a);
-    init_parent(ok, b);
+    rec[SeamLayout::ROW_B + k] = edge_root(ok, ok ? root_at(0, k) : 0);
+    rec[SeamLayout::ROW_T + k] = edge_root(ok, ok ? root_at(h - 1, k) : 0);
     const bool n = ok && ((sm.mb[(h - 1) * STRIPS + (k >> 5)] >> (2 * (k & 31) + 1)) & 1ull);
     const uint32_t nb = __ballot_sync(FULL, n);
     if (lane == 0) rec[SeamLayout::N_BITS + (k >> 5)] = (int32_t)nb;
@@ -276,28 +307,45 @@ __device__ __forceinline__ void sw_label_tile(const SwRep& R, int t, uint64_t sw
     add_observables<LABEL_THREADS>(n_eq, cnt, q, q <= QREG ? q : 0, oslot, red, hist);
   }
   __syncthreads();
+  // 6. edge-root bits into the (now free) pair-list slot; each thread reads
+  //    and next clears only its own word
+  slot[threadIdx.x] = (int32_t)ls.edge_bits[threadIdx.x];
 }
 
 // One tile of the fused flip step (see k_fused.cu).  All threads of the CTA
 // call it; it synchronises the CTA internally and on return.
+// Site ownership of the flip: thread (warp, lane) owns, in each of four
+// passes j, the eight sites (row 8j + warp, columns 8 lane .. 8 lane + 7) of
+// the tile; their tile roots are one 16-byte word per pass.
+constexpr int FLIP_PASSES = TILE_SITES / (8 * LABEL_THREADS);
+static_assert(FLIP_PASSES * 8 * LABEL_THREADS == TILE_SITES && TILE_W == 256, "site ownership");
+
+// Local root (16 bits) of site i (0..7) of a pass word.
+__device__ __forceinline__ int root_in(const uint4& v, int i) {
+  const uint32_t wv = (i < 2) ? v.x : (i < 4) ? v.y : (i < 6) ? v.z : v.w;
+  return (int)((wv >> (16 * (i & 1))) & 0xFFFFu);
+}
+
+// The pass words of the calling thread.
+struct RootsInRegs {
+  uint4 r4[FLIP_PASSES];
+  __device__ __forceinline__ uint4 get(int j) const { return r4[j]; }
+};
+// Steps 2-5 of the flip of tile t (see k_fused.cu) given the tile roots of
+// the calling thread's sites.  All threads of the CTA call it; it ends with a
+// barrier.
 // FEW: the few-cluster update (Sec. IV, variant (c)).  Only clusters whose
 // global root has its bit set in `sel` (seeded clusters) move: with FLIP draw
 // w of the root, iff (uint64)w.y < P, to state (s + 1 + F_{q-1}(w.x)) mod q,
 // s being the cluster's current state (read at the tile root).
-template <bool FEW = false>
-__device__ __forceinline__ void sw_flip_tile(const SwRep& R, int t, uint64_t sweep, int limit, FlipTileSmem& fs,
-                                             const uint32_t* __restrict__ sel = nullptr, uint64_t P = 0) {
-  // Thread t owns, in each of four passes j, the eight sites
-  // (row 8j + t/32, columns 8(t%32) .. 8(t%32)+7) of the tile: one 16-byte
-  // load of tile roots and one 8-byte store of spins per pass.
-  constexpr int PASSES = TILE_SITES / (8 * LABEL_THREADS);
-  static_assert(PASSES * 8 * LABEL_THREADS == TILE_SITES && TILE_W == 256, "site ownership");
+template <bool FEW, class Roots>
+__device__ __forceinline__ void flip_tile_core(const SwRep& R, int t, uint64_t sweep, int limit, FlipTileSmem& fs,
+                                               const Roots& roots, const uint32_t* __restrict__ sel, uint64_t P) {
+  constexpr int PASSES = FLIP_PASSES;
   uint16_t* rlist = fs.rlist;
   uint8_t* ns = fs.ns;
-  uint32_t* edge_mark = fs.edge_mark;
   int* warp_cnt = fs.warp_cnt;
   int8_t* __restrict__ spins = R.spins;
-  const uint16_t* __restrict__ lroot = R.lroot;
   int32_t* __restrict__ gpar = R.gpar;
   const Grid& g = R.g;
   const int q = R.q;
@@ -309,56 +357,20 @@ __device__ __forceinline__ void sw_flip_tile(const SwRep& R, int t, uint64_t swe
   const int h = min(TILE_H, L - y0), w = min(TILE_W, L - x0);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int lx0 = 8 * lane;
+  // the tile's edge-root bits, left by the labeling kernel
+  fs.edge_bits[threadIdx.x] = (uint32_t)__ldcg(R.s.roots + (int64_t)t * TILE_SITES + threadIdx.x);
 
-  // 1. tile roots of my sites (w is a multiple of 4: a group of eight sites is
-  //    either wholly inside, or its first four are); read through L2 because a
-  //    persistent kernel wrote them on other SMs
-  uint4 r4[PASSES];
-#pragma unroll
-  for (int j = 0; j < PASSES; ++j) {
-    const int ly = 8 * j + warp;
-    const uint16_t* src = lroot + (int64_t)(y0 + ly) * L + x0 + lx0;
-    r4[j] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
-    // 16-byte loads need L % 8 == 0; L % 4 == 0 always allows 8-byte loads
-    if (ly < h && lx0 + 8 <= w) {
-      if ((L & 7) == 0) {
-        r4[j] = __ldcg(reinterpret_cast<const uint4*>(src));
-      } else {
-        const uint2 a = __ldcg(reinterpret_cast<const uint2*>(src)), b = __ldcg(reinterpret_cast<const uint2*>(src + 4));
-        r4[j] = make_uint4(a.x, a.y, b.x, b.y);
-      }
-    } else if (ly < h && lx0 + 4 <= w) {
-      const uint2 v = __ldcg(reinterpret_cast<const uint2*>(src));
-      r4[j].x = v.x;
-      r4[j].y = v.y;
-    }
-  }
-  for (int k = threadIdx.x; k < TILE_SITES / 32; k += LABEL_THREADS) edge_mark[k] = 0u;
-  __syncthreads();
-
-  auto root_of = [&](int j, int i) -> int {   // site i (0..7) of pass j
-    const uint32_t wv = (i < 2) ? r4[j].x : (i < 4) ? r4[j].y : (i < 6) ? r4[j].z : r4[j].w;
-    return (int)((wv >> (16 * (i & 1))) & 0xFFFFu);
-  };
-
-  // 2. roots on the tile edge (their clusters may continue outside the tile);
-  //    3. my roots
+  // 2. my roots
   uint32_t mine = 0;   // bit 8j + i: site i of pass j is a root
 #pragma unroll
   for (int j = 0; j < PASSES; ++j) {
     const int ly = 8 * j + warp;
-    const bool edge_row = ly == 0 || ly == h - 1;
-    int marked = -1;   // last root this lane marked (runs of equal roots along a row)
+    const uint4 rv = roots.get(j);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int lx = lx0 + i;
       if (ly >= h || lx >= w) continue;
-      const int r = root_of(j, i);
-      if ((edge_row || lx == 0 || lx == w - 1) && r != marked) {
-        atomicOr(&edge_mark[r >> 5], 1u << (r & 31));
-        marked = r;
-      }
-      if (r == ly * TILE_W + lx) mine |= 1u << (8 * j + i);
+      if (root_in(rv, i) == ly * TILE_W + lx) mine |= 1u << (8 * j + i);
     }
   }
   const int cnt = __popc(mine);
@@ -377,19 +389,21 @@ __device__ __forceinline__ void sw_flip_tile(const SwRep& R, int t, uint64_t swe
     n_roots += warp_cnt[k];
   }
   base += incl - cnt;
-  while (mine) {
+  while (mine) {   // the tile's root list, edge roots flagged
     const int b = __ffs(mine) - 1;
     mine &= mine - 1;
-    rlist[base++] = (uint16_t)((8 * (b >> 3) + warp) * TILE_W + lx0 + (b & 7));
+    const int r = (8 * (b >> 3) + warp) * TILE_W + lx0 + (b & 7);
+    rlist[base++] = (uint16_t)r | (((fs.edge_bits[r >> 5] >> (r & 31)) & 1u) ? EDGE_ROOT : (uint16_t)0);
   }
   __syncthreads();
 
   // 4. one draw per tile root, keyed by its cluster's final root
   const uint32_t klo = (uint32_t)seed, khi = (uint32_t)(seed >> 32);
   for (int k = threadIdx.x; k < n_roots; k += LABEL_THREADS) {
-    const int r = rlist[k];
+    const int raw = rlist[k];
+    const int r = raw & ROOT_MASK;
     int Rg = tile_global(r, y0, x0, L);
-    if ((edge_mark[r >> 5] >> (r & 31)) & 1u) Rg = g_find(gpar, Rg, limit, err);
+    if (raw & EDGE_ROOT) Rg = g_find(gpar, Rg, limit, err);
     if (FEW) {
       // the cluster's current state, read at the tile root (this tile's own
       // site: step 5 rewrites it only after a barrier)
@@ -411,14 +425,15 @@ __device__ __forceinline__ void sw_flip_tile(const SwRep& R, int t, uint64_t swe
   for (int j = 0; j < PASSES; ++j) {
     const int ly = 8 * j + warp;
     if (ly >= h || lx0 + 4 > w) continue;
+    const uint4 rv = roots.get(j);
     uint32_t lo = 0, hi = 0;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) lo |= (uint32_t)ns[root_of(j, i)] << (8 * i);
+    for (int i = 0; i < 4; ++i) lo |= (uint32_t)ns[root_in(rv, i)] << (8 * i);
     int8_t* dst = spins + (int64_t)(y0 + ly) * L + x0 + lx0;
     *reinterpret_cast<uint32_t*>(dst) = lo;   // 4-byte aligned: L % 4 == 0
     if (lx0 + 8 <= w) {
 #pragma unroll
-      for (int i = 0; i < 4; ++i) hi |= (uint32_t)ns[root_of(j, 4 + i)] << (8 * i);
+      for (int i = 0; i < 4; ++i) hi |= (uint32_t)ns[root_in(rv, 4 + i)] << (8 * i);
       *reinterpret_cast<uint32_t*>(dst + 4) = hi;
     }
   }
@@ -471,17 +486,55 @@ __device__ __forceinline__ void observe_tile(const SwRep& R, int t, uint64_t don
   __syncthreads();
 }
 
+
+// The flip of tile t with the tile roots loaded into registers (one CTA per
+// tile; also the batch kernels).
+template <bool FEW = false>
+__device__ __forceinline__ void sw_flip_tile(const SwRep& R, int t, uint64_t sweep, int limit, FlipTileSmem& fs,
+                                             const uint32_t* __restrict__ sel = nullptr, uint64_t P = 0) {
+  const uint16_t* __restrict__ lroot = R.lroot;
+  const int L = R.g.W;
+  const int ty = t / R.g.tiles_x, tx = t - ty * R.g.tiles_x;
+  const int y0 = ty * TILE_H, x0 = tx * TILE_W;
+  const int h = min(TILE_H, L - y0), w = min(TILE_W, L - x0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lx0 = 8 * lane;
+  // 1. tile roots of my sites (w is a multiple of 4: a group of eight sites is
+  //    either wholly inside, or its first four are); read through L2 because a
+  //    persistent kernel wrote them on other SMs
+  RootsInRegs roots;
+#pragma unroll
+  for (int j = 0; j < FLIP_PASSES; ++j) {
+    const int ly = 8 * j + warp;
+    const uint16_t* src = lroot + (int64_t)(y0 + ly) * L + x0 + lx0;
+    uint4 v = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+    // 16-byte loads need L % 8 == 0; L % 4 == 0 always allows 8-byte loads
+    if (ly < h && lx0 + 8 <= w) {
+      if ((L & 7) == 0) {
+        v = __ldcg(reinterpret_cast<const uint4*>(src));
+      } else {
+        const uint2 a = __ldcg(reinterpret_cast<const uint2*>(src)), b = __ldcg(reinterpret_cast<const uint2*>(src + 4));
+        v = make_uint4(a.x, a.y, b.x, b.y);
+      }
+    } else if (ly < h && lx0 + 4 <= w) {
+      const uint2 a = __ldcg(reinterpret_cast<const uint2*>(src));
+      v.x = a.x;
+      v.y = a.y;
+    }
+    roots.r4[j] = v;
+  }
+  flip_tile_core<FEW>(R, t, sweep, limit, fs, roots, sel, P);
+}
+
 // ---------------------------------------------------------------------------
 // Few-cluster seed selection (Sec. IV, variant (c)): the seed of block b of
 // the ell x ell block grid (side B = L / ell) is (bx B + F_B(w.x),
 // by B + F_B(w.y)) with w the SEED draw (b, sweep); the bit of its cluster's
-// global root is set in `sel`.  Runs between the merge and the flip.  One
-// warp per seed: the seed's tile root is an edge root (its cluster may leave
-// the tile) iff it appears in the tile's seam record; then its global root is
-// found on gpar, otherwise the tile root is the cluster's root.
+// global root is set in `sel`.  Runs between the merge and the flip.  If the
+// seed's tile root is an edge root (its cluster may leave the tile), its
+// global root is found on gpar; otherwise the tile root is the cluster's root.
 __device__ __forceinline__ void few_select_seed(const SwRep& R, int ell, int64_t b, uint64_t sweep, uint32_t* sel,
                                                 int limit) {
-  const int lane = threadIdx.x & 31;
   const Grid& g = R.g;
   const int L = g.W;
   const int B = L / ell;
@@ -490,19 +543,12 @@ __device__ __forceinline__ void few_select_seed(const SwRep& R, int ell, int64_t
                          (uint32_t)R.seed, (uint32_t)(R.seed >> 32));
   const int x = bx * B + state_of(w.x, B), y = by * B + state_of(w.y, B);
   const int ty = y / TILE_H, tx = x / TILE_W;
-  const int t = ty * g.tiles_x + tx;
-  const int y0 = ty * TILE_H, x0 = tx * TILE_W;
   const int r = R.lroot[(int64_t)y * L + x];
-  const int G = tile_global(r, y0, x0, L);
-  const int32_t* rec = R.s.seams + (int64_t)t * SeamLayout::INTS;
-  bool edge = false;
-  for (int k = lane; k < TILE_H; k += 32) edge |= rec[SeamLayout::COL_L + k] == G || rec[SeamLayout::COL_R + k] == G;
-  for (int k = lane; k < TILE_W; k += 32) edge |= rec[SeamLayout::ROW_B + k] == G || rec[SeamLayout::ROW_T + k] == G;
-  edge = __any_sync(FULL, edge);
-  if (lane == 0) {
-    const int root = edge ? g_find(R.gpar, G, limit, R.s.err) : G;
-    atomicOr(sel + (root >> 5), 1u << (root & 31));
-  }
+  const int G = tile_global(r, ty * TILE_H, tx * TILE_W, L);
+  const int32_t* edge_bits = R.s.roots + (int64_t)(ty * g.tiles_x + tx) * TILE_SITES;
+  const bool edge = (__ldcg(edge_bits + (r >> 5)) >> (r & 31)) & 1;
+  const int root = edge ? g_find(R.gpar, G, limit, R.s.err) : G;
+  atomicOr(sel + (root >> 5), 1u << (root & 31));
 }
 
 }  // namespace swccl

@@ -9,15 +9,17 @@
 //              and east column beyond it), draws the tile's bonds (rule of
 //              Eq. 7, Sec. II.A) into shared memory, labels the tile with
 //              the engine of tile_engine.cuh, and writes each site's tile
-//              root as a 16-bit local index, the seam record of the tile, and
-//              a parent entry gpar[r] = r for every tile root r on the tile's
-//              edge.  It also counts, for the spins it read (the result of
-//              the previous sweep), the bonds joining equal spins and the
-//              sites per state, the observables of that sweep.
+//              root as a 16-bit local index (the root's own entry flagged
+//              if its component touches the tile edge), the seam record of
+//              the tile, and a parent entry gpar[r] = r for every tile root
+//              r on the tile's edge.  It also counts, for the spins it read
+//              (the result of the previous sweep), the bonds joining equal
+//              spins and the sites per state, the observables of that sweep.
 //  k_merge     (k_label.cu) joins tile roots across seams on gpar.
-//  k_sw_flip   one CTA per tile: lists the tile's roots; a root on the tile
-//              edge looks up its final root R in gpar, any other root is its
-//              own final root; each root draws its cluster's new state once
+//  k_sw_flip   one CTA per tile: lists the tile's roots; a flagged root
+//              (on the tile edge) looks up its final root R in gpar, any
+//              other root is its own final root; each root draws its
+//              cluster's new state once
 //              (FLIP draw keyed by R, Sec. II.D) and every site copies the
 //              state of its tile root.
 //
@@ -33,7 +35,7 @@
 namespace swccl {
 
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(LABEL_THREADS)
+__global__ void __launch_bounds__(LABEL_THREADS, 4)
 k_sw_label(SwRep R, const SwCtl* __restrict__ ctl, int obs_cap) {
   __shared__ LabelTileSmem ls;
   const uint64_t sweep = ctl->sweep;
@@ -57,9 +59,8 @@ constexpr int SELECT_THREADS = 256;
 
 __global__ void __launch_bounds__(SELECT_THREADS)
 k_few_select(SwRep R, const SwCtl* __restrict__ ctl, int ell, uint32_t* sel, int limit) {
-  const int64_t b = blockIdx.x * (int64_t)(SELECT_THREADS / 32) + (threadIdx.x >> 5);
-  if (b >= (int64_t)ell * ell) return;   // whole warps leave together
-  few_select_seed(R, ell, b, ctl->sweep, sel, limit);
+  const int64_t b = blockIdx.x * (int64_t)SELECT_THREADS + threadIdx.x;   // one thread per seed
+  if (b < (int64_t)ell * ell) few_select_seed(R, ell, b, ctl->sweep, sel, limit);
 }
 
 // ---------------------------------------------------------------------------
@@ -164,7 +165,7 @@ cudaError_t launch_few_select(const uint16_t* lroot, int32_t* gpar, const Grid& 
   const int limit = (int)std::min<int64_t>(g.n_sites() + 64, (int64_t)1 << 30);
   const SwRep R = make_rep(nullptr, const_cast<uint16_t*>(lroot), gpar, nullptr, g, s, 2, 0, seed);
   const int64_t seeds = (int64_t)ell * ell;
-  const int64_t blocks = (seeds + SELECT_THREADS / 32 - 1) / (SELECT_THREADS / 32);
+  const int64_t blocks = (seeds + SELECT_THREADS - 1) / SELECT_THREADS;
   k_few_select<<<(unsigned)blocks, SELECT_THREADS, 0, st>>>(R, ctl, ell, sel, limit);
   return cudaGetLastError();
 }

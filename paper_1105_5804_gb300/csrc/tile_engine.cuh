@@ -39,7 +39,7 @@ static_assert(LABEL_THREADS == TILE_W, "one warp per 32-column strip");
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
 struct TileSmem {
-  int par[TILE_SITES];
+  alignas(16) int par[TILE_SITES];   // 16-byte aligned: read as int4 when the tile roots are written
   unsigned long long mb[TILE_H * STRIPS];
   int warp_count[STRIPS];
   int warp_roots[LABEL_THREADS / 32];
