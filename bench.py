@@ -28,7 +28,27 @@ L_BENCH, Q_BENCH, SEED_BENCH = 16384, 2, 7
 # the paper's number for this metric and workload: q = 2 at beta_c, L = 16384,
 # self-labeling + sewing on a Tesla M2070, 3.573 ns per site and sweep (Table I)
 PAPER_SITE_UPDATES_PER_NS = 1.0 / 3.573
-WORKLOAD = "sw_ising_q2_L16384_beta_c_hot_start_seed7"
+WORKLOAD = "sw_ising_q2_L%d_beta_c_hot_start_seed7"
+# DRAM traffic of k_sw_label per site from one ncu capture at L = 8192 (the
+# full-size launch is too large to capture under ncu's replay; the traffic
+# grows with the sites processed): (dram__bytes_read.sum +
+# dram__bytes_write.sum) / sites = (99.43 + 168.08) MB / 67,108,864, summary in
+# profiles/k_sw_label_k_sw_flip_k_merge_L8192.md.  Valid only for the kernel
+# sources it was taken with (hash below); otherwise the line reports null.
+LABEL_TRAFFIC_BYTES_PER_SITE = 3.986
+LABEL_TRAFFIC_SOURCES = ("fused_tile.cuh", "tile_engine.cuh", "k_fused.cu", "swccl_device.cuh", "swccl_shared.h")
+LABEL_TRAFFIC_SOURCE_HASH = "75e3fa03d31990ac"
+
+
+def _label_traffic(N):
+    """Per-launch DRAM bytes of k_sw_label scaled from the capture, or None
+    if the kernel's sources changed since."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in LABEL_TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_1105_5804_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return LABEL_TRAFFIC_BYTES_PER_SITE * N if h.hexdigest()[:16] == LABEL_TRAFFIC_SOURCE_HASH else None
 # Algorithmic HBM bytes per site of one fused sweep: k_sw_label reads the
 # int8 spins (1 B) and writes a 16-bit tile root (2 B); k_sw_flip reads the
 # root (2 B) and writes the spins (1 B).  Seam records and edge-root entries
@@ -187,7 +207,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / max(args.steps, 1), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "L": L_BENCH, "q": Q_BENCH, "beta": KC_ISING,
+        "config": {"workload": WORKLOAD % L_BENCH, "L": L_BENCH, "q": Q_BENCH, "beta": KC_ISING,
                    "sample_L": L, "note": "each step is one oracle sweep of an L=1024 sample"},
         "cpu_baseline": {"value": value, "unit": "site-updates/ns", "cores": 1, "kind": "oracle",
                          "sample": "one serial oracle sweep of the L=1024 q=2 Ising lattice at beta_c per step",
@@ -528,9 +548,10 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak",
         "vs_baseline": value / PAPER_SITE_UPDATES_PER_NS,
         "dtype": "int32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "L": L, "q": q, "beta": KC_ISING, "convention": "ising (K=2 beta J)",
+        "config": {"workload": WORKLOAD % L, "L": L, "q": q, "beta": KC_ISING, "convention": "ising (K=2 beta J)",
                    "start": "hot", "seed": SEED_BENCH, "replicas": world, "parallelism": "replicas",
-                   "l2": "inputs larger than L2 (int32 labels 1 GiB, spins 256 MiB per replica)"},
+                   "l2": "inputs larger than L2 (spins %d MiB, 16-bit tile roots %d MiB per replica)"
+                         % (N >> 20, (2 * N) >> 20)},
         "clocks": clk,
         "gpu_launches": 4 * args.steps,
         "e2e": {"value": e2e_value, "unit": "site-updates/ns", "h2d_bytes_per_step": N,
@@ -538,7 +559,8 @@ def run_ours(args):
                 "path": "sw_set_spins(host) + sw_sweep(1) + sw_observables + sw_get_spins(host), pinned buffers"},
         "roofline": {"bound": "alu", "kernel": "k_sw_label", "achieved": philox_achieved / 1e9,
                      "peak": philox_peak / 1e9, "unit": "Gcall/s (Philox4x32-10)",
-                     "frac": philox_achieved / philox_peak, "traffic": None,
+                     "frac": philox_achieved / philox_peak, "traffic": _label_traffic(N),
+                     "traffic_note": "bytes per launch: ncu dram read+write per site at L=8192 x sites",
                      "peak_kind": "measured in this run: Philox-only kernel, 8 CTAs x 256 threads per SM",
                      "work_model": "%.1f Philox calls/site x %d sites per launch; the kernel also labels its "
                                    "tile, which shares the integer pipes" % (LABEL_PHILOX_CALLS_PER_SITE, N),
