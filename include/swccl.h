@@ -231,12 +231,13 @@ uint64_t sw_prob_threshold(double p);
  * F_q of word 0) and the observables (n_eq over the 3N bonds, then n_k) are
  * as on the square lattice.  Hot start: INIT draw of site i as in 2D.
  * Requires X, Y, Z >= 1 with X*Y*Z <= 2^30, 2 <= q <= 127, T <= 2^32.  The
- * library owns the device memory: 5 bytes per site plus the observable
- * ring.  NULL on failure (see sw_last_error).  Each sweep is four kernels
- * (brick-local union-find, face merge, flip, observables), replayed as a
+ * library owns the device memory: about 23 bytes per site (spins, brick
+ * roots, parent array, labeling scratch) plus the observable ring.  NULL on failure (see sw_last_error).  Each sweep is
+ * three kernels (brick-local union-find with the previous sweep's
+ * observables, face merge, flip) and a counter advance, replayed as a
  * captured CUDA graph unless timing is on. */
 typedef struct sw3_handle sw3_handle;
-#define SW3_N_PHASES 4   /* local, merge, flip, observables */
+#define SW3_N_PHASES 4   /* local (+ observables), merge, flip, advance */
 
 sw3_handle* sw3_create(int X, int Y, int Z, int q, uint64_t T, uint64_t seed, int hot_start, void* stream);
 sw3_handle* sw3_create_ex(int X, int Y, int Z, int q, double beta, double J, int convention, uint64_t seed,

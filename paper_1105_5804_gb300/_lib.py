@@ -21,7 +21,7 @@ SW_BATCH_PHASES, SW_BATCH_PERSISTENT = 0, 1
 SW_UPDATE_SW, SW_UPDATE_FEW = 0, 1
 PHASE_NAMES = ("activate", "local", "merge", "roots", "flip")
 SW3_N_PHASES = 4
-PHASE_NAMES3 = ("local", "merge", "flip", "observe")
+PHASE_NAMES3 = ("local", "merge", "flip", "advance")
 
 
 class SwcclError(RuntimeError):

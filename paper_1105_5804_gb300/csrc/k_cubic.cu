@@ -7,22 +7,28 @@
 // Philox call per site (tag BOND3, counter (i, sweep), word = direction) and
 // open iff the two spins are equal and the word is below T (Eq. 7).
 //
-// One sweep is four kernels:
-//  k3_local    one CTA per 32 x 8 x 16 brick: draws the bonds of its sites,
-//              joins those inside the brick with union-find in shared memory
-//              (larger root hooked under the smaller, so a brick root is the
-//              brick component's smallest index), and writes for every site
-//              gpar[i] = global index of its brick root;
+// One sweep is three kernels and an advance, the structure of the fused
+// square-lattice sweep (k_fused.cu) carried to bricks of 32 x 8 x 16 sites:
+//  k3_local    one CTA per brick: draws the bonds of its sites, labels the
+//              brick with the square-lattice tile engine (each warp sweeps an
+//              (x, z) plane; +y bonds and wraps joined with shared-memory
+//              unions; larger root hooked under the smaller, so a brick root
+//              is the brick component's smallest index), writes each site's brick root as
+//              a 16-bit local index, marks the roots whose component touches
+//              the brick's faces (edge roots: bit words per brick, and a
+//              parent entry gpar[G] = G at their global index G), and counts
+//              the observables of the spins it read (the previous sweep's);
 //  k3_merge    one thread per site on a brick face: redraws the face bond
-//              (the draws are counter-based) and, if open, joins the two
-//              sides on gpar with global atomics;
-//  k3_flip     every site finds its cluster root R on gpar and takes the
-//              state F_q of the FLIP draw keyed by R (Sec. II.D);
-//  k3_observe  bonds joining equal spins and sites per state of the new
-//              spins, into the sweep's observable slot; then k3_advance.
-// HBM traffic per site: spins read 1 B, gpar written 4 B (local), gpar read
-// 4 B and spins written 1 B (flip), spins read 1 B (observe), plus the face
-// sites' neighbours and the root chains.
+//              (the draws are counter-based) and, if open, joins the brick
+//              roots on its two ends on gpar with global atomics;
+//  k3_flip     one CTA per brick: lists the brick's roots; an edge root looks
+//              up its cluster root R on gpar, any other root is its own
+//              cluster's root; one FLIP draw per root (keyed by R, Sec. II.D)
+//              gives the state every site of the brick component takes.
+//  k3_observe  counts the observables of the last sweep when they are read.
+// HBM traffic per site: spins read 1 B and brick roots written 2 B (local),
+// brick roots read 2 B and spins written 1 B (flip), plus the face sites,
+// the edge-root bits (1/8 B) and the sparse parent entries.
 #include "fused_tile.cuh"
 
 namespace swccl {
@@ -63,43 +69,187 @@ __device__ __forceinline__ uint4 bond3_words(int64_t i, uint64_t sweep, uint64_t
   return draw((uint32_t)i, sweep, TAG_BOND3, seed);
 }
 
-__global__ void __launch_bounds__(B3_THREADS)
-k3_local(const int8_t* __restrict__ spins, int32_t* __restrict__ gpar, Box3 b, uint64_t T, uint64_t seed,
-         const SwCtl* __restrict__ ctl, int* err) {
-  __shared__ int par[B3_SITES];
-  const int t = blockIdx.x;
-  const int tbx = t % b.bx, tby = (t / b.bx) % b.by, tbz = t / (b.bx * b.by);
-  const int x0 = tbx * B3X, y0 = tby * B3Y, z0 = tbz * B3Z;
-  const int w = min(B3X, b.X - x0), h = min(B3Y, b.Y - y0), dpt = min(B3Z, b.Z - z0);
-  for (int l = threadIdx.x; l < B3_SITES; l += B3_THREADS) par[l] = l;
+constexpr int B3_EDGE_WORDS = B3_SITES / 32;   // edge-root bits of one brick
+
+struct Brick {
+  int tbx, tby, tbz, x0, y0, z0, w, h, d;
+};
+
+__device__ __forceinline__ Brick brick_of(const Box3& b, int t) {
+  Brick k;
+  k.tbx = t % b.bx;
+  k.tby = (t / b.bx) % b.by;
+  k.tbz = t / (b.bx * b.by);
+  k.x0 = k.tbx * B3X;
+  k.y0 = k.tby * B3Y;
+  k.z0 = k.tbz * B3Z;
+  k.w = min(B3X, b.X - k.x0);
+  k.h = min(B3Y, b.Y - k.y0);
+  k.d = min(B3Z, b.Z - k.z0);
+  return k;
+}
+
+// Global index of local index l of brick k (l = (lz B3Y + ly) B3X + lx).
+__device__ __forceinline__ int64_t brick_global(const Box3& b, const Brick& k, int l) {
+  return site3(b, k.x0 + l % B3X, k.y0 + (l / B3X) % B3Y, k.z0 + l / (B3X * B3Y));
+}
+
+// Spins of a brick and of its +x, +y, +z neighbour faces in shared memory:
+// entry (lz, ly, lx) for lx <= w, ly <= h, lz <= d (one past the brick's end
+// is the neighbouring brick's face, or the periodic wrap).
+constexpr int SP_X = B3X + 1, SP_Y = B3Y + 1, SP_Z = B3Z + 1;
+constexpr int SP_SIZE = SP_X * SP_Y * SP_Z;
+__device__ __forceinline__ int sp_at(int lx, int ly, int lz) { return (lz * SP_Y + ly) * SP_X + lx; }
+
+// A brick is labeled by the square-lattice tile engine (tile_engine.cuh):
+// with row = lz and strip = ly its local index (lz B3Y + ly) B3X + lx is the
+// engine's row * TILE_W + strip * 32 + lane, so each warp sweeps its (x, z)
+// plane along z (the +x bonds are the engine's east bonds, the +z bonds its
+// north bonds).  The +y bonds between the planes, and the periodic wraps of
+// an axis one brick long, are joined afterwards with shared-memory unions.
+static_assert(B3X == 32 && B3Y == STRIPS && B3Z <= TILE_H && B3X * B3Y == TILE_W, "brick = engine tile");
+
+struct Local3Smem {
+  TileSmem tile;
+  uint32_t edge[B3_EDGE_WORDS];
+  uint32_t ybits[B3Z * B3Y];     // open +y bond joined inside the brick, bit = lx
+  uint32_t xwrap[B3Z * B3Y];     // open +x bond wrapping inside the brick (one brick along x)
+  uint32_t zwrap[B3Y];           // open +z bond of the last plane wrapping inside the brick
+  unsigned long long red[(1 + QREG) * (B3_THREADS / 32)];
+  int hist[128];
+  int8_t sp[SP_SIZE];
+};
+
+__global__ void __launch_bounds__(B3_THREADS, 4)
+k3_local(const int8_t* __restrict__ spins, uint16_t* __restrict__ lroot, int32_t* __restrict__ gpar,
+         uint32_t* __restrict__ edge_words, int32_t* __restrict__ scratch, Box3 b, int q, uint64_t T, uint64_t seed,
+         const SwCtl* __restrict__ ctl, int64_t* obs, int obs_cap, int* err) {
+  __shared__ Local3Smem ls;
+  TileSmem& sm = ls.tile;
+  int* par = sm.par;
+  int8_t* sp = ls.sp;
+  const Brick k = brick_of(b, blockIdx.x);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lx = lane, ly = warp;
+  if (threadIdx.x == 0) sm.n_hooked = 0;
+  for (int j = threadIdx.x; j < B3_EDGE_WORDS; j += B3_THREADS) ls.edge[j] = 0u;
+  for (int j = threadIdx.x; j < 128; j += B3_THREADS) ls.hist[j] = 0;
+  if (threadIdx.x < B3Y) ls.zwrap[threadIdx.x] = 0u;
+  // 0. the brick's spins and the three neighbour faces (no edges or corners:
+  //    bonds are along the axes); all loads of a thread before its stores
+  constexpr int SP_ITERS = (SP_SIZE + B3_THREADS - 1) / B3_THREADS;
+  int8_t v[SP_ITERS];
+#pragma unroll
+  for (int it = 0; it < SP_ITERS; ++it) {
+    const int e = threadIdx.x + it * B3_THREADS;
+    const int ex = e % SP_X, ey = (e / SP_X) % SP_Y, ez = e / (SP_X * SP_Y);
+    const bool need = e < SP_SIZE && ex <= k.w && ey <= k.h && ez <= k.d &&
+                      (int)(ex == k.w) + (int)(ey == k.h) + (int)(ez == k.d) <= 1;
+    const int x = k.x0 + ex, y = k.y0 + ey, z = k.z0 + ez;
+    v[it] = need ? spins[site3(b, x == b.X ? 0 : x, y == b.Y ? 0 : y, z == b.Z ? 0 : z)] : (int8_t)0;
+  }
+#pragma unroll
+  for (int it = 0; it < SP_ITERS; ++it) {
+    const int e = threadIdx.x + it * B3_THREADS;
+    if (e < SP_SIZE) sp[e] = v[it];
+  }
   __syncthreads();
   const uint64_t sweep = ctl->sweep;
-  const uint64_t Tp = T >= (1ull << 32) ? ~0ull : T;   // p = 1: every equal bond opens
-  const int lx = threadIdx.x & (B3X - 1), ly = threadIdx.x / B3X;
-  if (lx < w && ly < h) {
-    for (int lz = 0; lz < dpt; ++lz) {
-      const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
-      const int64_t i = site3(b, x, y, z);
-      const int s = spins[i];
-      const uint4 wd = bond3_words(i, sweep, T, seed);
-      const int l = (lz * B3Y + ly) * B3X + lx;
+  const bool do_obs = sweep > 0 && ctl->obs_done != (long long)(sweep - 1);
+  const uint32_t Tw = (uint32_t)T;
+  const bool all_open = T >= (1ull << 32), none_open = T == 0;
+  const bool col = lx < k.w && ly < k.h;
+  long long n_eq = 0;
+  int cnt[QREG];
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        int nx, ny, nz;
-        if (!bond3(spins, b, x, y, z, d, s, wd, Tp, nx, ny, nz)) continue;
-        if (nx / B3X != tbx || ny / B3Y != tby || nz / B3Z != tbz) continue;   // face bond: k3_merge
-        sm_union(par, l, ((nz - z0) * B3Y + (ny - y0)) * B3X + (nx - x0), B3_SITES, err);
+  for (int j = 0; j < QREG; ++j) cnt[j] = 0;
+  // 1. bonds of every site (plane ly = warp, lane lx, rows lz); observables
+  //    of the spins read
+  for (int lz = 0; lz < k.d; ++lz) {
+    bool o0 = false, o1 = false, o2 = false;
+    if (col) {
+      const int s = sp[sp_at(lx, ly, lz)];
+      const bool e0 = sp[sp_at(lx + 1, ly, lz)] == s, e1 = sp[sp_at(lx, ly + 1, lz)] == s,
+                 e2 = sp[sp_at(lx, ly, lz + 1)] == s;
+      if (do_obs) {
+        n_eq += (int)e0 + (int)e1 + (int)e2;
+        if (q <= QREG) {
+#pragma unroll
+          for (int j = 0; j < QREG; ++j) cnt[j] += (s == j);
+        } else {
+          atomicAdd(&ls.hist[s], 1);
+        }
       }
+      if (!none_open && (e0 || e1 || e2)) {
+        if (all_open) {
+          o0 = e0;
+          o1 = e1;
+          o2 = e2;
+        } else {
+          const uint4 wd = draw((uint32_t)site3(b, k.x0 + lx, k.y0 + ly, k.z0 + lz), sweep, TAG_BOND3, seed);
+          o0 = e0 && wd.x < Tw;
+          o1 = e1 && wd.y < Tw;
+          o2 = e2 && wd.z < Tw;
+        }
+      }
+    }
+    // inside the brick: +x to lane lx+1, +z to row lz+1 (engine); +y to plane
+    // ly+1 (union below); wraps of an axis one brick long (union below)
+    const uint32_t east = __ballot_sync(FULL, o0 && lx + 1 < k.w);
+    const uint32_t north = __ballot_sync(FULL, o2 && lz + 1 < k.d);
+    const uint32_t ybit = __ballot_sync(FULL, o1 && (ly + 1 < k.h || b.by == 1));
+    const uint32_t xw = __ballot_sync(FULL, o0 && lx + 1 == k.w && b.bx == 1);
+    const uint32_t zw = __ballot_sync(FULL, o2 && lz + 1 == k.d && b.bz == 1);
+    if (lane == 0) {
+      sm.mb[lz * STRIPS + ly] = spread_even(east) | (spread_even(north) << 1);
+      ls.ybits[lz * B3Y + ly] = ybit;
+      ls.xwrap[lz * B3Y + ly] = xw;
+      if (zw) ls.zwrap[ly] = zw;
     }
   }
   __syncthreads();
-  if (lx < w && ly < h) {
-    for (int lz = 0; lz < dpt; ++lz) {
+  // 2. the engine labels the brick's planes and joins them along z
+  int32_t* slot = scratch + (int64_t)blockIdx.x * 2 * TILE_SITES;
+  tile_engine(sm, k.d, TILE_W, slot, slot + TILE_SITES, err);
+  // 3. +y bonds and wraps
+  for (int lz = 0; lz < k.d; ++lz) {
+    const int l = (lz * B3Y + ly) * B3X + lx;
+    if ((ls.ybits[lz * B3Y + ly] >> lx) & 1u)
+      sm_union(par, l, ly + 1 < k.h ? l + B3X : l - ly * B3X, B3_SITES, err);
+    if ((ls.xwrap[lz * B3Y + ly] >> lx) & 1u) sm_union(par, l, l - lx, B3_SITES, err);
+    if (lz + 1 == k.d && ((ls.zwrap[ly] >> lx) & 1u)) sm_union(par, l, l - lz * B3Y * B3X, B3_SITES, err);
+  }
+  __syncthreads();
+  uint32_t* edge = ls.edge;
+  int* hist = ls.hist;
+  unsigned long long* red = ls.red;
+  // 4. brick roots (16-bit local index) of every site; edge roots marked
+  if (col) {
+    for (int lz = 0; lz < k.d; ++lz) {
       const int l = (lz * B3Y + ly) * B3X + lx;
       const int r = sm_find(par, l, B3_SITES, err);
-      const int rx = r % B3X, ry = (r / B3X) % B3Y, rz = r / (B3X * B3Y);
-      gpar[site3(b, x0 + lx, y0 + ly, z0 + lz)] = (int32_t)site3(b, x0 + rx, y0 + ry, z0 + rz);
+      lroot[site3(b, k.x0 + lx, k.y0 + ly, k.z0 + lz)] = (uint16_t)r;
+      if (lx == 0 || lx == k.w - 1 || ly == 0 || ly == k.h - 1 || lz == 0 || lz == k.d - 1)
+        atomicOr(&edge[r >> 5], 1u << (r & 31));
     }
+  }
+  __syncthreads();
+  // 5. parent entries of edge roots; the brick's edge bits for the flip
+  if (col) {
+    for (int lz = 0; lz < k.d; ++lz) {
+      const int l = (lz * B3Y + ly) * B3X + lx;
+      if (par[l] == l && ((edge[l >> 5] >> (l & 31)) & 1u)) {
+        const int64_t G = site3(b, k.x0 + lx, k.y0 + ly, k.z0 + lz);
+        gpar[G] = (int32_t)G;
+      }
+    }
+  }
+  for (int j = threadIdx.x; j < B3_EDGE_WORDS; j += B3_THREADS)
+    edge_words[(int64_t)blockIdx.x * B3_EDGE_WORDS + j] = edge[j];
+  if (do_obs) {
+    unsigned long long* oslot =
+        reinterpret_cast<unsigned long long*>(obs + (int64_t)((sweep - 1) % (uint64_t)obs_cap) * (q + 1));
+    add_observables<B3_THREADS>(n_eq, cnt, q, q <= QREG ? q : 0, oslot, red, hist);
   }
 }
 
@@ -109,8 +259,8 @@ __device__ __forceinline__ int face_coord(int k, int extent, int brick) {
   return min((k + 1) * brick, extent) - 1;
 }
 
-__global__ void k3_merge(const int8_t* __restrict__ spins, int32_t* gpar, Box3 b, uint64_t T, uint64_t seed,
-                         const SwCtl* __restrict__ ctl, int limit, int* err) {
+__global__ void k3_merge(const int8_t* __restrict__ spins, const uint16_t* __restrict__ lroot, int32_t* gpar, Box3 b,
+                         uint64_t T, uint64_t seed, const SwCtl* __restrict__ ctl, int limit, int* err) {
   const int64_t nfx = b.bx > 1 ? (int64_t)b.bx * b.Y * b.Z : 0;
   const int64_t nfy = b.by > 1 ? (int64_t)b.X * b.by * b.Z : 0;
   const int64_t nfz = b.bz > 1 ? (int64_t)b.X * b.Y * b.bz : 0;
@@ -144,25 +294,90 @@ __global__ void k3_merge(const int8_t* __restrict__ spins, int32_t* gpar, Box3 b
     const int s = spins[i];
     const uint4 wd = bond3_words(i, sweep, T, seed);
     int nx, ny, nz;
-    if (bond3(spins, b, x, y, z, d, s, wd, Tp, nx, ny, nz))
-      g_union(gpar, (int)i, (int)site3(b, nx, ny, nz), limit, err);
+    if (bond3(spins, b, x, y, z, d, s, wd, Tp, nx, ny, nz)) {
+      // the brick roots on the two ends (both edge roots)
+      const Brick ka = brick_of(b, ((z / B3Z) * b.by + y / B3Y) * b.bx + x / B3X);
+      const Brick kb = brick_of(b, ((nz / B3Z) * b.by + ny / B3Y) * b.bx + nx / B3X);
+      const int ra = lroot[i], rb = lroot[site3(b, nx, ny, nz)];
+      g_union(gpar, (int)brick_global(b, ka, ra), (int)brick_global(b, kb, rb), limit, err);
+    }
   }
 }
 
-__global__ void k3_flip(int8_t* __restrict__ spins, int32_t* gpar, int64_t n, int q, uint64_t seed,
-                        const SwCtl* __restrict__ ctl, int limit, int* err) {
+__global__ void __launch_bounds__(B3_THREADS, 4)
+k3_flip(int8_t* __restrict__ spins, const uint16_t* __restrict__ lroot, int32_t* gpar,
+        const uint32_t* __restrict__ edge_words, Box3 b, int q, uint64_t seed, const SwCtl* __restrict__ ctl,
+        int limit, int* err) {
+  __shared__ uint16_t rlist[B3_SITES];
+  __shared__ uint8_t ns[B3_SITES];
+  __shared__ uint32_t edge[B3_EDGE_WORDS];
+  __shared__ int warp_cnt[B3_THREADS / 32];
+  const Brick k = brick_of(b, blockIdx.x);
   const uint64_t sweep = ctl->sweep;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int R = g_find(gpar, (int)i, limit, err);
-    spins[i] = (int8_t)state_of(draw((uint32_t)R, sweep, TAG_FLIP, seed).x, q);
+  for (int j = threadIdx.x; j < B3_EDGE_WORDS; j += B3_THREADS)
+    edge[j] = edge_words[(int64_t)blockIdx.x * B3_EDGE_WORDS + j];
+  const int lx = threadIdx.x & (B3X - 1), ly = threadIdx.x / B3X;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool col = lx < k.w && ly < k.h;
+  // 1. brick roots of my sites (two per register), and which of them are roots
+  uint32_t rr[B3Z / 2];
+  uint32_t mine = 0;
+#pragma unroll
+  for (int lz = 0; lz < B3Z; ++lz) {
+    uint32_t r = 0;
+    if (col && lz < k.d) {
+      r = lroot[site3(b, k.x0 + lx, k.y0 + ly, k.z0 + lz)];
+      if ((int)r == (lz * B3Y + ly) * B3X + lx) mine |= 1u << lz;
+    }
+    if (lz & 1) rr[lz >> 1] |= r << 16;
+    else rr[lz >> 1] = r;
+  }
+  // 2. the brick's root list
+  const int cnt = __popc(mine);
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) warp_cnt[warp] = incl;
+  __syncthreads();
+  int base = 0, n_roots = 0;
+#pragma unroll
+  for (int j = 0; j < B3_THREADS / 32; ++j) {
+    base += (j < warp) ? warp_cnt[j] : 0;
+    n_roots += warp_cnt[j];
+  }
+  base += incl - cnt;
+  while (mine) {
+    const int lz = __ffs(mine) - 1;
+    mine &= mine - 1;
+    rlist[base++] = (uint16_t)((lz * B3Y + ly) * B3X + lx);
+  }
+  __syncthreads();
+  // 3. one draw per brick root, keyed by its cluster's root
+  for (int j = threadIdx.x; j < n_roots; j += B3_THREADS) {
+    const int r = rlist[j];
+    int R = (int)brick_global(b, k, r);
+    if ((edge[r >> 5] >> (r & 31)) & 1u) R = g_find(gpar, R, limit, err);
+    ns[r] = (uint8_t)state_of(draw((uint32_t)R, sweep, TAG_FLIP, seed).x, q);
+  }
+  __syncthreads();
+  // 4. every site takes its brick root's state
+  if (col) {
+#pragma unroll
+    for (int lz = 0; lz < B3Z; ++lz) {
+      if (lz >= k.d) break;
+      const int r = (rr[lz >> 1] >> (16 * (lz & 1))) & 0xFFFF;
+      spins[site3(b, k.x0 + lx, k.y0 + ly, k.z0 + lz)] = (int8_t)ns[r];
+    }
   }
 }
 
 constexpr int OBS3_THREADS = 256;
 
 __global__ void __launch_bounds__(OBS3_THREADS)
-k3_observe(const int8_t* __restrict__ spins, Box3 b, int q, const SwCtl* __restrict__ ctl, int64_t* obs,
-           int obs_cap) {
+k3_observe(const int8_t* __restrict__ spins, Box3 b, int q, SwCtl* __restrict__ ctl, int64_t* obs, int obs_cap) {
   __shared__ unsigned long long red[(1 + QREG) * (OBS3_THREADS / 32)];
   __shared__ int hist[128];
   for (int k = threadIdx.x; k < 128; k += OBS3_THREADS) hist[k] = 0;
@@ -187,22 +402,37 @@ k3_observe(const int8_t* __restrict__ spins, Box3 b, int q, const SwCtl* __restr
       atomicAdd(&hist[s], 1);
     }
   }
+  const uint64_t done = ctl->sweep - 1;
   unsigned long long* slot =
-      reinterpret_cast<unsigned long long*>(obs + (int64_t)(ctl->sweep % (uint64_t)obs_cap) * (q + 1));
+      reinterpret_cast<unsigned long long*>(obs + (int64_t)(done % (uint64_t)obs_cap) * (q + 1));
   add_observables<OBS3_THREADS>(n_eq, cnt, q, q <= QREG ? q : 0, slot, red, hist);
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctl->obs_done = (long long)done;
 }
 
-// Zero the next sweep's observable slot, then advance the sweep counter.
+// End of a sweep: clear the observable slot of the sweep just done (the next
+// sweep's k3_local, or k3_observe, fills it), then advance the counter.
 __global__ void k3_advance(SwCtl* ctl, int64_t* obs, int obs_cap, int q) {
-  const uint64_t s = ctl->sweep + 1;
+  const uint64_t s = ctl->sweep;
   if ((int)threadIdx.x <= q) obs[(int64_t)(s % (uint64_t)obs_cap) * (q + 1) + threadIdx.x] = 0;
   __syncthreads();
-  if (threadIdx.x == 0) ctl->sweep = s;
+  if (threadIdx.x == 0) ctl->sweep = s + 1;
 }
 
-__global__ void k3_labels(int32_t* gpar, int32_t* out, int64_t n, int limit, int* err) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = g_find(gpar, (int)i, limit, err);
+// Canonical labels of the last sweep: the cluster root of every site's brick root.
+__global__ void k3_labels(const uint16_t* __restrict__ lroot, int32_t* gpar, const uint32_t* __restrict__ edge_words,
+                          Box3 b, int32_t* out, int limit, int* err) {
+  const int64_t n = b.n();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % b.X);
+    const int64_t yz = i / b.X;
+    const int y = (int)(yz % b.Y), z = (int)(yz / b.Y);
+    const int t = ((z / B3Z) * b.by + y / B3Y) * b.bx + x / B3X;
+    const Brick k = brick_of(b, t);
+    const int r = lroot[i];
+    int R = (int)brick_global(b, k, r);
+    if ((edge_words[(int64_t)t * B3_EDGE_WORDS + (r >> 5)] >> (r & 31)) & 1u) R = g_find(gpar, R, limit, err);
+    out[i] = R;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -223,35 +453,46 @@ static unsigned stride_blocks(int64_t n, int threads) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, 152 * 16));
 }
 
-cudaError_t launch_sweep3(int8_t* spins, int32_t* gpar, const Box3& b, int q, uint64_t T, uint64_t seed, SwCtl* ctl,
-                          int64_t* obs, int obs_cap, cudaStream_t st, cudaEvent_t* ev) {
+int64_t edge_words3(const Box3& b) { return b.n_bricks() * B3_EDGE_WORDS; }
+
+int64_t scratch_ints3(const Box3& b) { return b.n_bricks() * 2 * TILE_SITES; }
+
+cudaError_t launch_sweep3(int8_t* spins, uint16_t* lroot, int32_t* gpar, uint32_t* edge_words, int32_t* scratch,
+                          const Box3& b, int q, uint64_t T, uint64_t seed, SwCtl* ctl, int64_t* obs, int obs_cap,
+                          cudaStream_t st, cudaEvent_t* ev) {
   cudaError_t e;
   int* err = &ctl->err;
-  const int64_t n = b.n();
   if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
-  k3_local<<<(unsigned)b.n_bricks(), B3_THREADS, 0, st>>>(spins, gpar, b, T, seed, ctl, err);
+  k3_local<<<(unsigned)b.n_bricks(), B3_THREADS, 0, st>>>(spins, lroot, gpar, edge_words, scratch, b, q, T, seed,
+                                                          ctl, obs, obs_cap, err);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
   const int64_t faces = (b.bx > 1 ? (int64_t)b.bx * b.Y * b.Z : 0) + (b.by > 1 ? (int64_t)b.X * b.by * b.Z : 0) +
                         (b.bz > 1 ? (int64_t)b.X * b.Y * b.bz : 0);
   if (faces > 0) {
-    k3_merge<<<stride_blocks(faces, 256), 256, 0, st>>>(spins, gpar, b, T, seed, ctl, limit3(b), err);
+    k3_merge<<<stride_blocks(faces, 256), 256, 0, st>>>(spins, lroot, gpar, b, T, seed, ctl, limit3(b), err);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
-  k3_flip<<<stride_blocks(n, 256), 256, 0, st>>>(spins, gpar, n, q, seed, ctl, limit3(b), err);
+  k3_flip<<<(unsigned)b.n_bricks(), B3_THREADS, 0, st>>>(spins, lroot, gpar, edge_words, b, q, seed, ctl, limit3(b),
+                                                         err);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[3], st)) != cudaSuccess) return e;
-  k3_observe<<<stride_blocks(n, OBS3_THREADS), OBS3_THREADS, 0, st>>>(spins, b, q, ctl, obs, obs_cap);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k3_advance<<<1, 128, 0, st>>>(ctl, obs, obs_cap, q);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[4], st)) != cudaSuccess) return e;
   return cudaSuccess;
 }
 
-cudaError_t launch_labels3(int32_t* gpar, int32_t* out, const Box3& b, int* err, cudaStream_t st) {
-  k3_labels<<<stride_blocks(b.n(), 256), 256, 0, st>>>(gpar, out, b.n(), limit3(b), err);
+cudaError_t launch_observe3(const int8_t* spins, const Box3& b, int q, SwCtl* ctl, int64_t* obs, int obs_cap,
+                            cudaStream_t st) {
+  k3_observe<<<stride_blocks(b.n(), OBS3_THREADS), OBS3_THREADS, 0, st>>>(spins, b, q, ctl, obs, obs_cap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_labels3(const uint16_t* lroot, int32_t* gpar, const uint32_t* edge_words, const Box3& b,
+                           int32_t* out, int* err, cudaStream_t st) {
+  k3_labels<<<stride_blocks(b.n(), 256), 256, 0, st>>>(lroot, gpar, edge_words, b, out, limit3(b), err);
   return cudaGetLastError();
 }
 

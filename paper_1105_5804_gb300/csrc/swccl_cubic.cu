@@ -34,7 +34,10 @@ struct sw3_handle {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int8_t* spins = nullptr;
-  int32_t* gpar = nullptr;   // union-find parents; also staging for host spins
+  uint16_t* lroot = nullptr;      // brick root of every site (16-bit local index)
+  int32_t* gpar = nullptr;        // parents of edge roots; also staging for host spins
+  uint32_t* edge_words = nullptr; // edge-root bits of every brick
+  int32_t* scratch = nullptr;     // labeling scratch of every brick
   SwCtl* ctl = nullptr;
   int64_t* obs = nullptr;
   uint64_t sweeps = 0, obs_read = 0;
@@ -42,6 +45,7 @@ struct sw3_handle {
   cudaGraphExec_t exec = nullptr;
   bool timing = false;
   bool labels_valid = false;
+  bool final_obs_pending = false;   // the last sweep's observables are counted when read
   std::vector<cudaEvent_t> ev_pending;   // SW3_N_PHASES + 1 per timed sweep
   std::vector<cudaEvent_t> ev_free;
 };
@@ -56,11 +60,22 @@ void free3(sw3_handle* h) {
   for (auto e : h->ev_pending) cudaEventDestroy(e);
   for (auto e : h->ev_free) cudaEventDestroy(e);
   cudaFree(h->spins);
+  cudaFree(h->lroot);
   cudaFree(h->gpar);
+  cudaFree(h->edge_words);
+  cudaFree(h->scratch);
   cudaFree(h->ctl);
   cudaFree(h->obs);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
+}
+
+// The next sweep's local step counts a sweep's observables; before they are
+// read or the spins replaced, count the last sweep's here.
+cudaError_t finish3(sw3_handle* h) {
+  if (!h->final_obs_pending) return cudaSuccess;
+  h->final_obs_pending = false;
+  return launch_observe3(h->spins, h->box, h->q, h->ctl, h->obs, OBS3_CAP, h->stream);
 }
 
 int status3(sw3_handle* h) {
@@ -103,6 +118,9 @@ sw3_handle* sw3_create(int X, int Y, int Z, int q, uint64_t T, uint64_t seed, in
     h->own_stream = true;
   }
   if (cudaMalloc(&h->spins, (size_t)n) != cudaSuccess || cudaMalloc(&h->gpar, (size_t)n * 4) != cudaSuccess ||
+      cudaMalloc(&h->lroot, (size_t)n * 2) != cudaSuccess ||
+      cudaMalloc(&h->edge_words, (size_t)edge_words3(h->box) * 4) != cudaSuccess ||
+      cudaMalloc(&h->scratch, (size_t)scratch_ints3(h->box) * 4) != cudaSuccess ||
       cudaMalloc(&h->ctl, sizeof(SwCtl)) != cudaSuccess ||
       cudaMalloc(&h->obs, (size_t)OBS3_CAP * (q + 1) * 8) != cudaSuccess) {
     cudaGetLastError();
@@ -147,14 +165,15 @@ int sw3_sweep(sw3_handle* h, int n) {
         }
         h->ev_pending.push_back(e);
       }
-      CK3(launch_sweep3(h->spins, h->gpar, h->box, h->q, h->T, h->seed, h->ctl, h->obs, OBS3_CAP, h->stream, ev));
+      CK3(launch_sweep3(h->spins, h->lroot, h->gpar, h->edge_words, h->scratch, h->box, h->q, h->T, h->seed, h->ctl,
+                        h->obs, OBS3_CAP, h->stream, ev));
       h->sweeps++;
     }
   } else {
     if (!h->exec) {
       CK3(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-      cudaError_t e = launch_sweep3(h->spins, h->gpar, h->box, h->q, h->T, h->seed, h->ctl, h->obs, OBS3_CAP,
-                                    h->stream, nullptr);
+      cudaError_t e = launch_sweep3(h->spins, h->lroot, h->gpar, h->edge_words, h->scratch, h->box, h->q, h->T,
+                                    h->seed, h->ctl, h->obs, OBS3_CAP, h->stream, nullptr);
       cudaGraph_t gr = nullptr;
       cudaError_t e2 = cudaStreamEndCapture(h->stream, &gr);
       if (e != cudaSuccess) {
@@ -171,6 +190,7 @@ int sw3_sweep(sw3_handle* h, int n) {
     }
   }
   h->labels_valid = true;
+  h->final_obs_pending = true;
   return SW_OK;
 }
 
@@ -182,6 +202,7 @@ int sw3_sync(sw3_handle* h) {
 int sw3_observables(sw3_handle* h, int64_t* out, int max_sweeps, int* n_written) {
   if (!h || (!out && max_sweeps > 0) || max_sweeps < 0) return fail3(SW_ERR_ARG, "sw3_observables: bad arguments");
   if (n_written) *n_written = 0;
+  CK3(finish3(h));
   int rc = status3(h);
   if (rc) return rc;
   if (h->sweeps - h->obs_read > (uint64_t)OBS3_CAP) h->obs_read = h->sweeps - OBS3_CAP;
@@ -210,6 +231,7 @@ int sw3_get_spins(sw3_handle* h, int8_t* dst, int is_device) {
 int sw3_set_spins(sw3_handle* h, const int8_t* src, int is_device) {
   if (!h || !src) return fail3(SW_ERR_ARG, "sw3_set_spins: bad arguments");
   const int64_t n = h->box.n();
+  CK3(finish3(h));   // the pending observables belong to the old spins
   int rc = status3(h);
   if (rc) return rc;
   // host input is staged in the parent array (4n bytes, rewritten by the
@@ -242,7 +264,7 @@ int sw3_labels(sw3_handle* h, int32_t* out, int is_device) {
   const int64_t n = h->box.n();
   int32_t* dst = out;
   if (!is_device) CK3(cudaMalloc(&dst, (size_t)n * 4));
-  cudaError_t e = launch_labels3(h->gpar, dst, h->box, &h->ctl->err, h->stream);
+  cudaError_t e = launch_labels3(h->lroot, h->gpar, h->edge_words, h->box, dst, &h->ctl->err, h->stream);
   if (e == cudaSuccess && !is_device) e = cudaMemcpyAsync(out, dst, (size_t)n * 4, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (!is_device) cudaFree(dst);

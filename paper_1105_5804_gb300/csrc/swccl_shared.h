@@ -149,11 +149,19 @@ cudaError_t launch_philox_probe(long long calls_per_thread, int blocks, uint32_t
 cudaError_t launch_check_spins(const int8_t* spins, int64_t n, int q, int* err, cudaStream_t st);
 cudaError_t launch_init_spins_n(int8_t* spins, int64_t n, int q, uint64_t seed, int hot, cudaStream_t st);
 // Simple-cubic sweep (k_cubic.cu).  ev, if not null, receives five events:
-// before the local step, merge, flip, observables, and after the advance.
+// before the local step, merge, flip, advance, and after the advance.  The
+// observables of a sweep are counted by the next sweep's local step, or by
+// launch_observe3 (the last sweep, when they are read).
 Box3 make_box3(int X, int Y, int Z);
-cudaError_t launch_sweep3(int8_t* spins, int32_t* gpar, const Box3& b, int q, uint64_t T, uint64_t seed, SwCtl* ctl,
-                          int64_t* obs, int obs_cap, cudaStream_t st, cudaEvent_t* ev);
-cudaError_t launch_labels3(int32_t* gpar, int32_t* out, const Box3& b, int* err, cudaStream_t st);
+int64_t edge_words3(const Box3& b);     // uint32 words of edge-root bits
+int64_t scratch_ints3(const Box3& b);   // int32 words of labeling scratch (pair lists, hook logs)
+cudaError_t launch_sweep3(int8_t* spins, uint16_t* lroot, int32_t* gpar, uint32_t* edge_words, int32_t* scratch,
+                          const Box3& b, int q, uint64_t T, uint64_t seed, SwCtl* ctl, int64_t* obs, int obs_cap,
+                          cudaStream_t st, cudaEvent_t* ev);
+cudaError_t launch_observe3(const int8_t* spins, const Box3& b, int q, SwCtl* ctl, int64_t* obs, int obs_cap,
+                            cudaStream_t st);
+cudaError_t launch_labels3(const uint16_t* lroot, int32_t* gpar, const uint32_t* edge_words, const Box3& b,
+                           int32_t* out, int* err, cudaStream_t st);
 
 cudaError_t launch_tile_label(const uint8_t* mask, int32_t* labels, const Grid& g,
                               const LabelScratch& s, cudaStream_t st);
