@@ -136,33 +136,47 @@ k3_local(const int8_t* __restrict__ spins, uint16_t* __restrict__ lroot, int32_t
   for (int j = threadIdx.x; j < 128; j += B3_THREADS) ls.hist[j] = 0;
   if (threadIdx.x < B3Y) ls.zwrap[threadIdx.x] = 0u;
   // 0. the brick's spins and the three neighbour faces (no edges or corners:
-  //    bonds are along the axes); all loads of a thread before its stores
-  constexpr int SP_ITERS = (SP_SIZE + B3_THREADS - 1) / B3_THREADS;
-  int8_t v[SP_ITERS];
+  //    bonds are along the axes).  Thread (lx, ly) loads its column, z face
+  //    included; threads 0..127 the +x face, all threads two entries of the
+  //    +y face; every load of a thread is issued before its stores.
+  const int64_t XY = (int64_t)b.X * b.Y;
+  const bool col = lx < k.w && ly < k.h;
+  const int64_t i0 = col ? site3(b, k.x0 + lx, k.y0 + ly, k.z0) : 0;   // column base, z = z0
+  const int zf = k.z0 + k.d == b.Z ? 0 : k.z0 + k.d;                      // z face (wrapped)
+  int8_t cz[B3Z + 1];
 #pragma unroll
-  for (int it = 0; it < SP_ITERS; ++it) {
-    const int e = threadIdx.x + it * B3_THREADS;
-    const int ex = e % SP_X, ey = (e / SP_X) % SP_Y, ez = e / (SP_X * SP_Y);
-    const bool need = e < SP_SIZE && ex <= k.w && ey <= k.h && ez <= k.d &&
-                      (int)(ex == k.w) + (int)(ey == k.h) + (int)(ez == k.d) <= 1;
-    const int x = k.x0 + ex, y = k.y0 + ey, z = k.z0 + ez;
-    v[it] = need ? spins[site3(b, x == b.X ? 0 : x, y == b.Y ? 0 : y, z == b.Z ? 0 : z)] : (int8_t)0;
+  for (int lz = 0; lz <= B3Z; ++lz) {
+    const bool in = col && lz < k.d;
+    cz[lz] = in ? spins[i0 + lz * XY] : (col && lz == k.d ? spins[site3(b, k.x0 + lx, k.y0 + ly, zf)] : (int8_t)0);
   }
+  const int xf = k.x0 + k.w == b.X ? 0 : k.x0 + k.w, yf = k.y0 + k.h == b.Y ? 0 : k.y0 + k.h;
+  const int fx_ly = threadIdx.x & (B3Y - 1), fx_lz = threadIdx.x >> 3;             // +x face: 8 x 16
+  const bool fx_in = threadIdx.x < B3Y * B3Z && fx_ly < k.h && fx_lz < k.d;
+  const int8_t fx = fx_in ? spins[site3(b, xf, k.y0 + fx_ly, k.z0 + fx_lz)] : (int8_t)0;
+  int8_t fy[2];                                                                       // +y face: 32 x 16
 #pragma unroll
-  for (int it = 0; it < SP_ITERS; ++it) {
-    const int e = threadIdx.x + it * B3_THREADS;
-    if (e < SP_SIZE) sp[e] = v[it];
+  for (int u = 0; u < 2; ++u) {
+    const int e = threadIdx.x + u * B3_THREADS, ex = e & (B3X - 1), ez = e >> 5;
+    fy[u] = (ex < k.w && ez < k.d) ? spins[site3(b, k.x0 + ex, yf, k.z0 + ez)] : (int8_t)0;
+  }
+  if (col) {   // only the brick's own columns: the faces at lx = w and ly = h are written below
+#pragma unroll
+    for (int lz = 0; lz <= B3Z; ++lz)
+      if (lz <= k.d) sp[sp_at(lx, ly, lz)] = cz[lz];
+  }
+  if (fx_in) sp[sp_at(k.w, fx_ly, fx_lz)] = fx;
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int e = threadIdx.x + u * B3_THREADS, ex = e & (B3X - 1), ez = e >> 5;
+    if (ex < k.w && ez < k.d) sp[sp_at(ex, k.h, ez)] = fy[u];
   }
   __syncthreads();
   const uint64_t sweep = ctl->sweep;
   const bool do_obs = sweep > 0 && ctl->obs_done != (long long)(sweep - 1);
   const uint32_t Tw = (uint32_t)T;
   const bool all_open = T >= (1ull << 32), none_open = T == 0;
-  const bool col = lx < k.w && ly < k.h;
   long long n_eq = 0;
-  int cnt[QREG];
-#pragma unroll
-  for (int j = 0; j < QREG; ++j) cnt[j] = 0;
+  unsigned long long cpack = 0;   // sites per state, 8 bits per state (q <= 8; at most 16 sites)
   // 1. bonds of every site (plane ly = warp, lane lx, rows lz); observables
   //    of the spins read
   for (int lz = 0; lz < k.d; ++lz) {
@@ -173,12 +187,8 @@ k3_local(const int8_t* __restrict__ spins, uint16_t* __restrict__ lroot, int32_t
                  e2 = sp[sp_at(lx, ly, lz + 1)] == s;
       if (do_obs) {
         n_eq += (int)e0 + (int)e1 + (int)e2;
-        if (q <= QREG) {
-#pragma unroll
-          for (int j = 0; j < QREG; ++j) cnt[j] += (s == j);
-        } else {
-          atomicAdd(&ls.hist[s], 1);
-        }
+        if (q <= QREG) cpack += 1ull << (8 * s);
+        else atomicAdd(&ls.hist[s], 1);
       }
       if (!none_open && (e0 || e1 || e2)) {
         if (all_open) {
@@ -186,7 +196,7 @@ k3_local(const int8_t* __restrict__ spins, uint16_t* __restrict__ lroot, int32_t
           o1 = e1;
           o2 = e2;
         } else {
-          const uint4 wd = draw((uint32_t)site3(b, k.x0 + lx, k.y0 + ly, k.z0 + lz), sweep, TAG_BOND3, seed);
+          const uint4 wd = draw((uint32_t)(i0 + lz * XY), sweep, TAG_BOND3, seed);
           o0 = e0 && wd.x < Tw;
           o1 = e1 && wd.y < Tw;
           o2 = e2 && wd.z < Tw;
@@ -228,7 +238,7 @@ k3_local(const int8_t* __restrict__ spins, uint16_t* __restrict__ lroot, int32_t
     for (int lz = 0; lz < k.d; ++lz) {
       const int l = (lz * B3Y + ly) * B3X + lx;
       const int r = sm_find(par, l, B3_SITES, err);
-      lroot[site3(b, k.x0 + lx, k.y0 + ly, k.z0 + lz)] = (uint16_t)r;
+      lroot[i0 + lz * XY] = (uint16_t)r;
       if (lx == 0 || lx == k.w - 1 || ly == 0 || ly == k.h - 1 || lz == 0 || lz == k.d - 1)
         atomicOr(&edge[r >> 5], 1u << (r & 31));
     }
@@ -238,15 +248,15 @@ k3_local(const int8_t* __restrict__ spins, uint16_t* __restrict__ lroot, int32_t
   if (col) {
     for (int lz = 0; lz < k.d; ++lz) {
       const int l = (lz * B3Y + ly) * B3X + lx;
-      if (par[l] == l && ((edge[l >> 5] >> (l & 31)) & 1u)) {
-        const int64_t G = site3(b, k.x0 + lx, k.y0 + ly, k.z0 + lz);
-        gpar[G] = (int32_t)G;
-      }
+      if (par[l] == l && ((edge[l >> 5] >> (l & 31)) & 1u)) gpar[i0 + lz * XY] = (int32_t)(i0 + lz * XY);
     }
   }
   for (int j = threadIdx.x; j < B3_EDGE_WORDS; j += B3_THREADS)
     edge_words[(int64_t)blockIdx.x * B3_EDGE_WORDS + j] = edge[j];
   if (do_obs) {
+    int cnt[QREG];
+#pragma unroll
+    for (int j = 0; j < QREG; ++j) cnt[j] = (int)((cpack >> (8 * j)) & 0xFFu);
     unsigned long long* oslot =
         reinterpret_cast<unsigned long long*>(obs + (int64_t)((sweep - 1) % (uint64_t)obs_cap) * (q + 1));
     add_observables<B3_THREADS>(n_eq, cnt, q, q <= QREG ? q : 0, oslot, red, hist);
