@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(BATCH_MERGE_THREADS) k_batch_merge(BatchView b
   merge_seam_bond(R.gpar, R.g, R.s, gt - R.tile0, threadIdx.x, true, b.limit);
 }
 
-__global__ void __launch_bounds__(LABEL_THREADS, 5) k_batch_flip(BatchView b, const BatchCtl* __restrict__ ctl) {
+__global__ void __launch_bounds__(LABEL_THREADS, 6) k_batch_flip(BatchView b, const BatchCtl* __restrict__ ctl) {
   __shared__ FlipTileSmem fs;
   const int gt = blockIdx.x;
   const SwRep& R = b.reps[b.tile_rep[gt]];

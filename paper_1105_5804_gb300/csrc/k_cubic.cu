@@ -314,7 +314,7 @@ __global__ void k3_merge(const int8_t* __restrict__ spins, const uint16_t* __res
   }
 }
 
-__global__ void __launch_bounds__(B3_THREADS, 4)
+__global__ void __launch_bounds__(B3_THREADS, 6)
 k3_flip(int8_t* __restrict__ spins, const uint16_t* __restrict__ lroot, int32_t* gpar,
         const uint32_t* __restrict__ edge_words, Box3 b, int q, uint64_t seed, const SwCtl* __restrict__ ctl,
         int limit, int* err) {

@@ -43,13 +43,13 @@ k_sw_label(SwRep R, const SwCtl* __restrict__ ctl, int obs_cap) {
   sw_label_tile(R, blockIdx.x, sweep, do_obs, obs_cap, ls);
 }
 
-__global__ void __launch_bounds__(LABEL_THREADS, 5)
+__global__ void __launch_bounds__(LABEL_THREADS, 6)
 k_sw_flip(SwRep R, const SwCtl* __restrict__ ctl, int limit) {
   __shared__ FlipTileSmem fs;
   sw_flip_tile(R, blockIdx.x, ctl->sweep, limit, fs);
 }
 
-__global__ void __launch_bounds__(LABEL_THREADS, 5)
+__global__ void __launch_bounds__(LABEL_THREADS, 6)
 k_sw_flip_few(SwRep R, const SwCtl* __restrict__ ctl, int limit, const uint32_t* __restrict__ sel, uint64_t P) {
   __shared__ FlipTileSmem fs;
   sw_flip_tile<true>(R, blockIdx.x, ctl->sweep, limit, fs, sel, P);
