@@ -2,10 +2,10 @@
 //
 // The tiles of all grids are numbered consecutively (tile_job[] maps a
 // global tile to its grid), and each step of the stand-alone labeling path
-// (local labeling, seam merge, root compression, site pass) runs as one
-// launch over all tiles of all grids.  A grid's labels are the same as
-// ccl_label gives for it alone: every grid has its own label array and
-// scratch, and the steps only ever touch the grid of the tile at hand.
+// (local labeling, seam merge, final labels) runs as one launch over all
+// tiles of all grids.  A grid's labels are the same as ccl_label gives for it
+// alone: every grid has its own label array and scratch, and the steps only
+// ever touch the grid of the tile at hand.
 #include "label_tile.cuh"
 
 namespace swccl {
@@ -14,7 +14,7 @@ __global__ void __launch_bounds__(LABEL_THREADS) k_cclb_tile(CclBatchView v) {
   __shared__ TileSmem sm;
   const int gt = blockIdx.x;
   const CclJob& J = v.jobs[v.tile_job[gt]];
-  ccl_label_tile(J.mask, J.labels, J.g, J.s, gt - J.tile0, sm);
+  ccl_label_tile<true>(J.mask, J.labels, J.g, J.s, gt - J.tile0, sm);
 }
 
 __global__ void __launch_bounds__(MERGE_PER_TILE) k_cclb_merge(CclBatchView v) {
@@ -23,24 +23,18 @@ __global__ void __launch_bounds__(MERGE_PER_TILE) k_cclb_merge(CclBatchView v) {
   merge_seam_bond(J.labels, J.g, J.s, gt - J.tile0, threadIdx.x, true, v.limit);
 }
 
-__global__ void __launch_bounds__(256) k_cclb_roots(CclBatchView v) {
+__global__ void __launch_bounds__(256) k_cclb_final(CclBatchView v) {
+  __shared__ int32_t table[TILE_SITES];
   const int gt = blockIdx.x;
   const CclJob& J = v.jobs[v.tile_job[gt]];
-  root_compress_tile(J.labels, J.s, gt - J.tile0, nullptr, 0, 0, 0, v.limit);
-}
-
-__global__ void __launch_bounds__(256) k_cclb_sites(CclBatchView v) {
-  const int gt = blockIdx.x;
-  const CclJob& J = v.jobs[v.tile_job[gt]];
-  site_compress_tile(J.labels, J.g, gt - J.tile0);
+  final_labels_tile(J.labels, J.g, J.s, gt - J.tile0, table, v.limit);
 }
 
 cudaError_t launch_ccl_batch(const CclBatchView& v, cudaStream_t st) {
   if (v.n_tiles == 0) return cudaSuccess;
   k_cclb_tile<<<v.n_tiles, LABEL_THREADS, 0, st>>>(v);
   k_cclb_merge<<<v.n_tiles, MERGE_PER_TILE, 0, st>>>(v);
-  k_cclb_roots<<<v.n_tiles, 256, 0, st>>>(v);
-  k_cclb_sites<<<v.n_tiles, 256, 0, st>>>(v);
+  k_cclb_final<<<v.n_tiles, 256, 0, st>>>(v);
   return cudaGetLastError();
 }
 

@@ -26,8 +26,13 @@
 //                 the final root is the cluster's minimum site index.  In a
 //                 Swendsen-Wang sweep the final roots also draw their
 //                 cluster's new state here (Sec. II.D), keyed by the root.
-//  k_site_compress  label[i] = label[label[i]] for every site (stand-alone
-//                 labeling only: leaves every label canonical).
+//  k_site_compress  label[i] = label[label[i]] for every site (the staged
+//                 sweep's dump of canonical labels).
+// The stand-alone labeling (launch_ccl) uses k_ccl_tile, a k_tile_label whose
+// non-root sites hold their tile root's local index (negated), then k_merge,
+// then k_ccl_final: per tile, each tile root finds its cluster root once and
+// every site takes its tile root's from a shared-memory table -- one pass
+// over the labels instead of a root pass and a site pass with gathers.
 #include "label_tile.cuh"
 
 namespace swccl {
@@ -42,6 +47,32 @@ k_tile_label(const uint8_t* __restrict__ mask, int32_t* __restrict__ labels, Gri
 cudaError_t launch_tile_label(const uint8_t* mask, int32_t* labels, const Grid& g,
                               const LabelScratch& s, cudaStream_t st) {
   k_tile_label<<<g.n_tiles(), LABEL_THREADS, 0, st>>>(mask, labels, g, s);
+  return cudaGetLastError();
+}
+
+// Stand-alone labeling: local labeling with local-root labels, then (after
+// the seam merge) the final labels of every tile in one pass.
+__global__ void __launch_bounds__(LABEL_THREADS)
+k_ccl_tile(const uint8_t* __restrict__ mask, int32_t* __restrict__ labels, Grid g, LabelScratch s) {
+  __shared__ TileSmem sm;
+  ccl_label_tile<true>(mask, labels, g, s, blockIdx.x, sm);
+}
+
+constexpr int FINAL_THREADS = 256;
+
+__global__ void __launch_bounds__(FINAL_THREADS)
+k_ccl_final(int32_t* labels, Grid g, LabelScratch s, int limit) {
+  __shared__ int32_t table[TILE_SITES];
+  final_labels_tile(labels, g, s, blockIdx.x, table, limit);
+}
+
+cudaError_t launch_ccl(const uint8_t* mask, int32_t* labels, const Grid& g, const LabelScratch& s, cudaStream_t st) {
+  k_ccl_tile<<<g.n_tiles(), LABEL_THREADS, 0, st>>>(mask, labels, g, s);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if ((e = launch_merge(labels, g, s, st)) != cudaSuccess) return e;
+  const int limit = (int)std::min<int64_t>(g.n_sites() + 64, (int64_t)1 << 30);
+  k_ccl_final<<<g.n_tiles(), FINAL_THREADS, 0, st>>>(labels, g, s, limit);
   return cudaGetLastError();
 }
 

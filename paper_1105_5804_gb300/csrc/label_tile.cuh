@@ -15,6 +15,12 @@ namespace swccl {
 // writes every site's label (global index of its tile root, the minimum
 // site index of its tile component), the tile's root list, and the seam
 // record (labels and outgoing bond bits of the four tile edges).
+// LOCAL (the stand-alone labeling path, finished by final_labels_tile): a
+// site that is not its tile's root gets -(r + 1), r its tile root's local
+// index, instead of the root's global index, and the root list holds local
+// indices.  Only tile roots' entries are global parent pointers, so the seam
+// merge and root lookups, which walk tile roots only, are unchanged.
+template <bool LOCAL = false>
 __device__ __forceinline__ void ccl_label_tile(const uint8_t* __restrict__ mask, int32_t* __restrict__ labels,
                                                const Grid& g, const LabelScratch& s, int t, TileSmem& sm) {
   int* par = sm.par;
@@ -62,7 +68,8 @@ __device__ __forceinline__ void ccl_label_tile(const uint8_t* __restrict__ mask,
     if (ly < h && lx < w) {
       const int p = par[sidx];
       const int r = par[p];
-      labels[(int64_t)(y0 + ly) * W + x0 + lx] = (y0 + (r >> TILE_W_LOG2)) * W + x0 + (r & (TILE_W - 1));
+      labels[(int64_t)(y0 + ly) * W + x0 + lx] =
+          (LOCAL && r != sidx) ? -(r + 1) : (y0 + (r >> TILE_W_LOG2)) * W + x0 + (r & (TILE_W - 1));
       if (r == sidx) mine |= 1u << j;
     }
   }
@@ -86,8 +93,7 @@ __device__ __forceinline__ void ccl_label_tile(const uint8_t* __restrict__ mask,
     const int j = __ffs(mine) - 1;
     mine &= mine - 1;
     const int sidx = threadIdx.x + j * LABEL_THREADS;
-    slot[base++] =
-        (y0 + (sidx >> TILE_W_LOG2)) * W + x0 + (sidx & (TILE_W - 1));
+    slot[base++] = LOCAL ? sidx : (y0 + (sidx >> TILE_W_LOG2)) * W + x0 + (sidx & (TILE_W - 1));
   }
 
   // 5. seam record
@@ -147,6 +153,36 @@ __device__ __forceinline__ void site_compress_tile(int32_t* __restrict__ labels,
       if (R != r) *p = R;
     }
   }
+}
+
+// Final labels of tile t for the stand-alone path (after the seam merge, on
+// labels written by ccl_label_tile<true>): each tile root (local root list)
+// finds its cluster root R on the label array and stores it in `table` at
+// its local index; then every site of the tile takes table[its tile root].
+// A tile root's entry receives R (smaller than any value other walks may
+// store there), so walks of other tiles through it stay valid.  All threads
+// of the CTA call it; it synchronises the CTA.
+__device__ __forceinline__ void final_labels_tile(int32_t* labels, const Grid& g, const LabelScratch& s, int t,
+                                                  int32_t* table /* shared, TILE_SITES */, int limit) {
+  const int ty = t / g.tiles_x, tx = t - ty * g.tiles_x;
+  const int y0 = ty * TILE_H, x0 = tx * TILE_W;
+  const int h = min(TILE_H, g.H - y0), w = min(TILE_W, g.W - x0);
+  const int n = __ldcg(s.root_counts + t);
+  const int32_t* list = s.roots + (int64_t)t * TILE_SITES;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const int r = __ldcg(list + k);   // local index
+    table[r] = g_find(labels, tile_global(r, y0, x0, g.W), limit, s.err);
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < TILE_SITES; k += blockDim.x) {
+    const int ly = k >> TILE_W_LOG2, lx = k & (TILE_W - 1);
+    if (ly < h && lx < w) {
+      int32_t* p = labels + (int64_t)(y0 + ly) * g.W + x0 + lx;
+      const int v = __ldcg(p);
+      *p = table[v < 0 ? -v - 1 : k];
+    }
+  }
+  __syncthreads();
 }
 
 }  // namespace swccl

@@ -536,10 +536,7 @@ int ccl_label_ws(const uint8_t* bond_mask, int32_t* labels, int H, int W, int pe
   if (!status) return fail(SW_ERR_CUDA, "ccl: cannot resolve the device status word");
   const LabelScratch s = carve_label_scratch(g, workspace, status);
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
-  CK(launch_tile_label(bond_mask, labels, g, s, st));
-  CK(launch_merge(labels, g, s, st));
-  CK(launch_root_compress(labels, g, s, nullptr, 0, 0, nullptr, st));
-  CK(launch_site_compress(labels, g.n_sites(), st));
+  CK(launch_ccl(bond_mask, labels, g, s, st));
   return SW_OK;
 }
 

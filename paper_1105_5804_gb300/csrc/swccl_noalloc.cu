@@ -84,10 +84,7 @@ extern "C" int ccl_label_noalloc(const uint8_t* bond_mask, int32_t* labels, int 
   const LabelScratch s = carve_label_scratch(g, ws, status);
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e;
-  if ((e = launch_tile_label(bond_mask, labels, g, s, st)) != cudaSuccess ||
-      (e = launch_merge(labels, g, s, st)) != cudaSuccess ||
-      (e = launch_root_compress(labels, g, s, nullptr, 0, 0, nullptr, st)) != cudaSuccess ||
-      (e = launch_site_compress(labels, g.n_sites(), st)) != cudaSuccess)
+  if ((e = launch_ccl(bond_mask, labels, g, s, st)) != cudaSuccess)
     return set_last_error(SW_ERR_CUDA, std::string("ccl_label_noalloc: launch: ") + cudaGetErrorString(e));
   return SW_OK;
 }

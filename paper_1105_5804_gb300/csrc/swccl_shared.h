@@ -172,6 +172,8 @@ cudaError_t launch_root_compress(int32_t* labels, const Grid& g, const LabelScra
                                  int8_t* spins, int q, uint64_t seed, const SwCtl* ctl,
                                  cudaStream_t st);
 cudaError_t launch_site_compress(int32_t* labels, int64_t n_sites, cudaStream_t st);
+// The stand-alone labeling of one grid: local labeling, seam merge, final labels.
+cudaError_t launch_ccl(const uint8_t* mask, int32_t* labels, const Grid& g, const LabelScratch& s, cudaStream_t st);
 
 cudaError_t launch_flip(int8_t* spins, const int32_t* labels, int L, int q, const SwCtl* ctl,
                         int64_t* obs_ring, int obs_cap, cudaStream_t st);
