@@ -420,10 +420,15 @@ def serving_secondary(torch, rates=(10, 30, 100, 300, 1000, 2000), seconds=1.0, 
     uniform in [256, 8192], windows of a blurred-noise 8-level image) and SW
     jobs (L uniform in [128, 4096], 10 sweeps at the Ising beta_c), 80:20,
     through the continuous-batching server with a 64 GiB budget and 4 slots.
-    Latency = completion (results on the device) - arrival."""
+    The image pool is in pinned host memory.  Latency = completion (results
+    on the device) - arrival."""
     from paper_1105_5804_gb300 import inputs, serve
-    pool = inputs.blurred_noise_image(8192, 8192, seed=0)
-    out = {"workload": "serve_label_HW256-8192_sw_L128-4096_poisson", "budget_gib": 64, "slots": 4, "rates": {}}
+    # request payloads arrive in pinned host memory (a server's receive buffers)
+    pool_pinned = torch.empty((8192, 8192), dtype=torch.uint8, pin_memory=True)
+    pool = pool_pinned.numpy()
+    pool[:] = inputs.blurred_noise_image(8192, 8192, seed=0)
+    out = {"workload": "serve_label_HW256-8192_sw_L128-4096_poisson", "budget_gib": 64, "slots": 4,
+           "payload": "pinned host image pool, windows uploaded by ccl_copy_pixels_2d", "rates": {}}
     # warm-up: allocator, graphs, libraries
     serve.run(serve.make_jobs(1000.0, 8, seed=99, image_pool=pool), serve.Server(64 << 30, slots=4))
     for rate in rates:

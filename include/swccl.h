@@ -363,6 +363,17 @@ int ccl_label_ws(const uint8_t* bond_mask, int32_t* labels, int H, int W, int pe
  * grid are closed. */
 int ccl_bonds_from_pixels(const uint8_t* px, uint8_t* mask, int H, int W, int periodic, void* stream);
 
+/* Copy an H x W uint8 image whose rows are `src_pitch` bytes apart (a window
+ * of a larger image) into the packed device array dst[H*W], asynchronously
+ * on `stream`, without a host-side repacking (no counterpart in the paper:
+ * the upload step of a labeling request).  src is host memory
+ * (src_is_device == 0; pinned memory makes the copy a DMA that overlaps the
+ * caller) or device memory.  The caller keeps src alive until the stream has
+ * passed the copy.  SW_ERR_ARG for null pointers, H or W < 1, or
+ * src_pitch < W. */
+int ccl_copy_pixels_2d(const uint8_t* src, int64_t src_pitch, uint8_t* dst, int H, int W, int src_is_device,
+                       void* stream);
+
 /* Critical bond percolation mask (p = 1/2) of seed k: each of the 2*H*W
  * bond bits is open iff its PERC draw is below 2^31.  mask: device,
  * ceil(H*W/4) bytes. */

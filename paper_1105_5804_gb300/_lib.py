@@ -68,6 +68,7 @@ def lib():
         "ccl_label_ws": ([vp, vp, i32, i32, i32, vp, i64, vp], i32),
         "ccl_bonds_from_pixels": ([vp, vp, i32, i32, i32, vp], i32),
         "ccl_perc_mask": ([u64, vp, i32, i32, vp], i32),
+        "ccl_copy_pixels_2d": ([vp, i64, vp, i32, i32, i32, vp], i32),
         "ccl_label_noalloc": ([vp, vp, i32, i32, i32, vp], i32),
         "ccl_status": ([], i32),
         "sw_probe_philox": ([i64, i32, vp, vp], i32),
@@ -394,6 +395,26 @@ def ccl_bonds_from_pixels(px, mask, H, W, periodic, stream=None):
                                        _dev(mask, torch.uint8, mask_bytes(N), "mask"), H, W,
                                        1 if periodic else 0, _stream(stream)))
     return mask
+
+
+def ccl_copy_pixels_2d(src, dst, stream=None):
+    """Upload an image window into the CUDA uint8 tensor ``dst`` (H*W
+    elements): ``src`` is a 2-D numpy uint8 array (a view of a larger image,
+    rows contiguous) or a 2-D CUDA tensor with unit column stride.  The copy
+    is asynchronous on ``stream``; keep ``src`` alive until it has run."""
+    import torch
+    if isinstance(src, torch.Tensor) and src.is_cuda:
+        if src.dim() != 2 or src.dtype != torch.uint8 or src.stride(1) != 1:
+            raise ValueError("src must be a 2-D uint8 CUDA tensor with unit column stride")
+        H, W = src.shape
+        ptr, pitch, dev = src.data_ptr(), src.stride(0), 1
+    else:
+        if not isinstance(src, np.ndarray) or src.ndim != 2 or src.dtype != np.uint8 or src.strides[1] != 1:
+            raise ValueError("src must be a 2-D uint8 numpy array with contiguous rows")
+        H, W = src.shape
+        ptr, pitch, dev = src.ctypes.data, src.strides[0], 0
+    _check(lib().ccl_copy_pixels_2d(ctypes.c_void_p(ptr), pitch, _dev(dst, torch.uint8, H * W, "dst"), H, W, dev,
+                                    _stream(stream)))
 
 
 def ccl_perc_mask(k, mask, H, W, stream=None):

@@ -563,6 +563,15 @@ int ccl_bonds_from_pixels(const uint8_t* px, uint8_t* mask, int H, int W, int pe
   return SW_OK;
 }
 
+int ccl_copy_pixels_2d(const uint8_t* src, int64_t src_pitch, uint8_t* dst, int H, int W, int src_is_device,
+                       void* stream) {
+  if (!src || !dst || H < 1 || W < 1 || src_pitch < W) return fail(SW_ERR_ARG, "ccl_copy_pixels_2d: bad arguments");
+  CK(cudaMemcpy2DAsync(dst, (size_t)W, src, (size_t)src_pitch, (size_t)W, (size_t)H,
+                       src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       static_cast<cudaStream_t>(stream)));
+  return SW_OK;
+}
+
 int ccl_perc_mask(uint64_t k, uint8_t* mask, int H, int W, void* stream) {
   int rc = ccl_validate(mask, mask, H, W);
   if (rc) return rc;

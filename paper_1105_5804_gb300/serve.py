@@ -17,7 +17,10 @@ never waited on) release their slot and memory.  Results do not depend on
 what else ran: every job's computation reads only its own inputs and seed.
 
 All computation runs in the library's kernels; torch provides device memory
-(its caching allocator) and streams.
+(its caching allocator) and streams.  A label job's pixels (a window of a
+host image, rows contiguous) are uploaded by one asynchronous 2-D copy on the
+group's stream; when the host image is in pinned memory the copy is a DMA
+that overlaps the server's work.
 """
 import collections
 import time
@@ -118,7 +121,13 @@ class Server:
             if kind == "label":
                 masks, labels = [], []
                 for j in jobs:
-                    px = torch.from_numpy(np.ascontiguousarray(j.pixels).reshape(-1)).to("cuda", non_blocking=False)
+                    # the window goes up as it is (rows of the source image), no host repacking;
+                    # the job keeps its host pixels until the group completes
+                    src = j.pixels
+                    if not (isinstance(src, np.ndarray) and src.ndim == 2 and src.strides[1] == 1):
+                        src = j.pixels = np.ascontiguousarray(src).reshape(j.H, j.W)
+                    px = torch.empty(j.H * j.W, dtype=torch.uint8, device="cuda")
+                    sw.ccl_copy_pixels_2d(src, px, st)
                     m = torch.empty(sw.mask_bytes(j.H * j.W), dtype=torch.uint8, device="cuda")
                     sw.ccl_bonds_from_pixels(px, m, j.H, j.W, False, st)
                     lab = torch.empty(j.H * j.W, dtype=torch.int32, device="cuda")

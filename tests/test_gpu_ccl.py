@@ -9,6 +9,8 @@ element (integer work: bit-exact).  At the 4096^2 size of the labeling
 workload, seeds 0..9 are compared in full and all 100 seeds are checked for
 the properties every canonical labeling has.
 """
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -203,3 +205,37 @@ def test_label_batch_rejects_small_workspace():
     lab = torch.zeros(64 * 64, dtype=torch.int32, device="cuda")
     with pytest.raises(sw.SwcclError):
         sw.ccl_label_batch([m], [lab], [64], [64], [True], ws)
+
+
+def test_copy_pixels_2d_windows_and_errors():
+    """The upload step of a labeling request: windows of a larger host image
+    (pageable and pinned) or device image land packed on the device, and the
+    labels of the uploaded window equal those of the packed copy."""
+    rng = np.random.default_rng(8)
+    big = rng.integers(0, 8, (300, 517)).astype(np.uint8)
+    pinned_t = torch.empty((300, 517), dtype=torch.uint8, pin_memory=True)
+    pinned = pinned_t.numpy()
+    pinned[:] = big
+    dev_big = torch.from_numpy(big).cuda()
+    for (y, x, H, W) in [(0, 0, 300, 517), (17, 33, 101, 203), (299, 516, 1, 1), (5, 0, 64, 517)]:
+        want = np.ascontiguousarray(big[y:y + H, x:x + W]).reshape(-1)
+        for src in (big[y:y + H, x:x + W], pinned[y:y + H, x:x + W], dev_big[y:y + H, x:x + W]):
+            dst = torch.zeros(H * W, dtype=torch.uint8, device="cuda")
+            sw.ccl_copy_pixels_2d(src, dst)
+            torch.cuda.synchronize()
+            assert np.array_equal(dst.cpu().numpy(), want), (y, x, H, W)
+        m = torch.empty(sw.mask_bytes(H * W), dtype=torch.uint8, device="cuda")
+        sw.ccl_bonds_from_pixels(dst, m, H, W, False)
+        lab = torch.empty(H * W, dtype=torch.int32, device="cuda")
+        sw.ccl_label(m, lab, H, W, False)
+        ref, _ = oracle.label(oracle.bonds_from_pixels(want.reshape(H, W), False), H, W, False)
+        assert np.array_equal(lab.cpu().numpy(), ref)
+    dst = torch.empty(16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(ValueError):
+        sw.ccl_copy_pixels_2d(big[:4, :4].T, dst)                     # columns not contiguous
+    with pytest.raises(ValueError):
+        sw.ccl_copy_pixels_2d(big[:4, :8], dst)                       # dst too small
+    L = sw.lib()
+    assert L.ccl_copy_pixels_2d(None, 4, ctypes.c_void_p(dst.data_ptr()), 4, 4, 0, None) == sw.SW_ERR_ARG
+    assert L.ccl_copy_pixels_2d(ctypes.c_void_p(big.ctypes.data), 3, ctypes.c_void_p(dst.data_ptr()), 4, 4, 0,
+                                None) == sw.SW_ERR_ARG                # pitch < W
