@@ -151,10 +151,76 @@ cudaError_t launch_sw_flip(int8_t* spins, const uint16_t* lroot, int32_t* gpar, 
   return cudaGetLastError();
 }
 
+// The same for L % 16 == 0 at HBM speed: a thread owns 16 columns (one
+// 16-byte word per row) of a band of OBS16_ROWS rows and keeps the row it
+// just read for the next row's north bonds, so every row is read once; the
+// east neighbour of its last column is the next lane's first byte.
+constexpr int OBS16_ROWS = 32;
+
+__global__ void __launch_bounds__(OBS_THREADS)
+k_observe16(const int8_t* __restrict__ spins, int L, int q, SwCtl* __restrict__ ctl, int64_t* __restrict__ obs,
+            int obs_cap) {
+  __shared__ unsigned long long red[(1 + QREG) * (OBS_THREADS / 32)];
+  __shared__ int hist[128];
+  for (int k = threadIdx.x; k < 128; k += OBS_THREADS) hist[k] = 0;
+  __syncthreads();
+  const uint64_t done = ctl->sweep - 1;
+  long long n_eq = 0;
+  int cnt[QREG];
+#pragma unroll
+  for (int k = 0; k < QREG; ++k) cnt[k] = 0;
+  const int lane = threadIdx.x & 31;
+  const int x = (blockIdx.x * OBS_THREADS + threadIdx.x) * 16;
+  const bool active = x < L;
+  const int xe = (x + 16 >= L) ? 0 : x + 16;        // east neighbour column of my last site
+  const int y0 = blockIdx.y * OBS16_ROWS, y1 = min(y0 + OBS16_ROWS, L);
+  auto row = [&](int y) -> uint4 {
+    return active ? *reinterpret_cast<const uint4*>(spins + (int64_t)y * L + x) : make_uint4(0u, 0u, 0u, 0u);
+  };
+  uint4 cur = row(y0);
+  for (int y = y0; y < y1; ++y) {
+    const uint4 nor = row(y + 1 == L ? 0 : y + 1);
+    // first byte east of my 16 columns: the next lane's, or (last lane / row end) a load
+    const uint32_t from_next = __shfl_down_sync(FULL, cur.x, 1) & 0xFFu;
+    const bool own_load = lane == 31 || xe == 0 || x + 16 >= L;
+    const uint32_t east_b = own_load ? (active ? (uint32_t)(uint8_t)spins[(int64_t)y * L + xe] : 0u) : from_next;
+    if (active) {
+      const uint32_t w[4] = {cur.x, cur.y, cur.z, cur.w}, nw[4] = {nor.x, nor.y, nor.z, nor.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t next = k < 3 ? w[k + 1] : east_b;
+        n_eq += __popc(eq4(w[k], (w[k] >> 8) | (next << 24))) + __popc(eq4(w[k], nw[k]));
+        if (q == 2) {
+          const int ones = __popc(w[k] & 0x01010101u);
+          cnt[1] += ones;
+          cnt[0] += 4 - ones;
+        } else if (q <= QREG) {
+#pragma unroll
+          for (int c = 0; c < QREG; ++c)
+            if (c < q) cnt[c] += __popc(eq4(w[k], 0x01010101u * (uint32_t)c));
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) atomicAdd(&hist[(w[k] >> (8 * j)) & 0xFF], 1);
+        }
+      }
+    }
+    cur = nor;
+  }
+  unsigned long long* oslot =
+      reinterpret_cast<unsigned long long*>(obs + (int64_t)(done % (uint64_t)obs_cap) * (q + 1));
+  add_observables<OBS_THREADS>(n_eq, cnt, q, q <= QREG ? q : 0, oslot, red, hist);
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) ctl->obs_done = (long long)done;
+}
+
 cudaError_t launch_observe(const int8_t* spins, int L, int q, SwCtl* ctl, int64_t* obs, int obs_cap,
                            cudaStream_t st) {
-  dim3 grid((unsigned)((L / 4 + OBS_THREADS - 1) / OBS_THREADS), (unsigned)((L + OBS_ROWS - 1) / OBS_ROWS));
-  k_observe<<<grid, OBS_THREADS, 0, st>>>(spins, L, q, ctl, obs, obs_cap);
+  if (L % 16 == 0) {
+    dim3 grid((unsigned)((L / 16 + OBS_THREADS - 1) / OBS_THREADS), (unsigned)((L + OBS16_ROWS - 1) / OBS16_ROWS));
+    k_observe16<<<grid, OBS_THREADS, 0, st>>>(spins, L, q, ctl, obs, obs_cap);
+  } else {
+    dim3 grid((unsigned)((L / 4 + OBS_THREADS - 1) / OBS_THREADS), (unsigned)((L + OBS_ROWS - 1) / OBS_ROWS));
+    k_observe<<<grid, OBS_THREADS, 0, st>>>(spins, L, q, ctl, obs, obs_cap);
+  }
   return cudaGetLastError();
 }
 
