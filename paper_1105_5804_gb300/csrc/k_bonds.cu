@@ -162,18 +162,58 @@ cudaError_t launch_init_spins_n(int8_t* spins, int64_t n, int q, uint64_t seed, 
   return cudaGetLastError();
 }
 
+// Spin checks and device copies run on the SMs, not on a copy engine: a
+// device-to-device copy on a copy engine queues behind host transfers that
+// other streams have in flight, while a kernel overlaps them.  Sixteen bytes
+// per thread and step where both pointers are 16-byte aligned.
+__device__ __forceinline__ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
 __global__ void k_check_spins(const int8_t* __restrict__ spins, int64_t n, int q, int* err) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x, t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const uint32_t qq = 0x01010101u * (uint32_t)q;   // a byte is valid iff it is below q (negative int8 >= 128)
+  int64_t head = 0;
+  if (aligned16(spins)) {
+    const uint4* v = reinterpret_cast<const uint4*>(spins);
+    bool bad = false;
+    for (int64_t i = t0; i < n / 16; i += stride) {
+      const uint4 w = v[i];
+      bad |= (__vcmpgeu4(w.x, qq) | __vcmpgeu4(w.y, qq) | __vcmpgeu4(w.z, qq) | __vcmpgeu4(w.w, qq)) != 0u;
+    }
+    if (bad) set_error(err, SW_ERR_ARG);
+    head = n / 16 * 16;
+  }
+  for (int64_t i = head + t0; i < n; i += stride) {
     const int s = spins[i];
     if (s < 0 || s >= q) set_error(err, SW_ERR_ARG);
   }
 }
 
+// dst = src if *ok_flag == 0 (left unchanged otherwise).
+__global__ void k_copy_if(int8_t* __restrict__ dst, const int8_t* __restrict__ src, int64_t n,
+                          const int* __restrict__ ok_flag) {
+  if (ok_flag && *ok_flag != 0) return;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x, t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t head = 0;
+  if (aligned16(dst) && aligned16(src)) {
+    const uint4* s4 = reinterpret_cast<const uint4*>(src);
+    uint4* d4 = reinterpret_cast<uint4*>(dst);
+    for (int64_t i = t0; i < n / 16; i += stride) d4[i] = s4[i];
+    head = n / 16 * 16;
+  }
+  for (int64_t i = head + t0; i < n; i += stride) dst[i] = src[i];
+}
+
+static unsigned sm_copy_blocks(int64_t n) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n / 16 + 255) / 256, 152 * 16));
+}
+
 cudaError_t launch_check_spins(const int8_t* spins, int64_t n, int q, int* err, cudaStream_t st) {
-  const int threads = 256;
-  const int64_t blocks = std::min<int64_t>((n + threads - 1) / threads, 152 * 16);
-  k_check_spins<<<(unsigned)std::max<int64_t>(blocks, 1), threads, 0, st>>>(spins, n, q, err);
+  k_check_spins<<<sm_copy_blocks(n), 256, 0, st>>>(spins, n, q, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_if(int8_t* dst, const int8_t* src, int64_t n, const int* ok_flag, cudaStream_t st) {
+  k_copy_if<<<sm_copy_blocks(n), 256, 0, st>>>(dst, src, n, ok_flag);
   return cudaGetLastError();
 }
 

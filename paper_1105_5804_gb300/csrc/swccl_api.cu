@@ -40,6 +40,7 @@ int cuda_fail(cudaError_t e, const char* what) {
   } while (0)
 
 constexpr int OBS_CAP = 4096;
+constexpr size_t READBACK_BYTES = 64 << 10;
 
 }  // namespace
 
@@ -90,6 +91,7 @@ struct sw_handle {
   int ell = 0;                       // few-cluster: ell x ell seed blocks
   uint64_t P_flip = 0;               // few-cluster: flip threshold
   uint32_t* sel = nullptr;           // few-cluster: seeded-cluster roots, one bit per site
+  void* readback = nullptr;          // mapped pinned host buffer for small reads (READBACK_BYTES)
   bool timing = false;
   bool dump_valid = false;  // mask/labels hold the last sweep's result
   std::vector<cudaEvent_t> ev_pending;   // SW_N_PHASES + 1 events per timed sweep
@@ -114,6 +116,7 @@ void free_handle(sw_handle* h) {
   cudaFree(h->scratch);
   cudaFree(h->ctl);
   cudaFree(h->chk);
+  if (h->readback) cudaFreeHost(h->readback);
   cudaFree(h->obs);
   cudaFree(h->lroot);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -175,10 +178,31 @@ cudaError_t finish_observables(sw_handle* h) {
   return launch_observe(h->spins, h->L, h->q, h->ctl, h->obs, OBS_CAP, h->stream);
 }
 
+// Synchronous copy ordered on the handle's stream (never on the legacy
+// default stream, which would also wait for every other blocking stream).
+cudaError_t copy_on(cudaStream_t st, void* dst, const void* src, size_t bytes, cudaMemcpyKind kind) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, kind, st);
+  return e != cudaSuccess ? e : cudaStreamSynchronize(st);
+}
+
+// Small device-to-host reads go through the handle's mapped pinned buffer:
+// a kernel stores the bytes there, the stream is synchronised, and the host
+// reads them.  A copy engine would queue them behind large host transfers
+// that other streams have in flight.
+cudaError_t read_small(sw_handle* h, void* dst, const void* src, size_t bytes) {
+  if (bytes > READBACK_BYTES) return copy_on(h->stream, dst, src, bytes, cudaMemcpyDeviceToHost);
+  void* dev_view = nullptr;
+  cudaError_t e = cudaHostGetDevicePointer(&dev_view, h->readback, 0);
+  if (e == cudaSuccess) e = launch_copy_if(static_cast<int8_t*>(dev_view), static_cast<const int8_t*>(src),
+                                           (int64_t)bytes, nullptr, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess) std::memcpy(dst, h->readback, bytes);
+  return e;
+}
+
 int check_device_status(sw_handle* h) {
-  CK(cudaStreamSynchronize(h->stream));
   SwCtl c;
-  CK(cudaMemcpy(&c, h->ctl, sizeof(c), cudaMemcpyDeviceToHost));
+  CK(read_small(h, &c, h->ctl, sizeof(c)));
   if (c.err) return fail(c.err, "a device-side consistency check failed in a sweep");
   return SW_OK;
 }
@@ -290,6 +314,7 @@ sw_handle* sw_create_threshold(int L, int q, uint64_t T, uint64_t seed, int hot_
   if ((e = cudaMalloc(&h->scratch, sbytes))) return bad(e, "label scratch");
   if ((e = cudaMalloc(&h->ctl, sizeof(SwCtl)))) return bad(e, "control block");
   if ((e = cudaMalloc(&h->chk, sizeof(int)))) return bad(e, "check word");
+  if ((e = cudaHostAlloc(&h->readback, READBACK_BYTES, cudaHostAllocMapped))) return bad(e, "read-back buffer");
   if ((e = cudaMalloc(&h->obs, (int64_t)OBS_CAP * (q + 1) * 8))) return bad(e, "observable ring");
   if ((e = cudaMalloc(&h->lroot, (N * 2 + 15) & ~15LL))) return bad(e, "tile roots");
   h->ls = carve_label_scratch(h->grid, h->scratch,
@@ -405,7 +430,7 @@ int sw_observables(sw_handle* h, int64_t* out, int max_sweeps, int* n_written) {
   while (done < cnt) {
     const int64_t slot = (int64_t)((h->obs_read + done) % OBS_CAP);
     const int64_t run = std::min<int64_t>(cnt - done, OBS_CAP - slot);
-    CK(cudaMemcpy(out + done * row, h->obs + slot * row, run * row * 8, cudaMemcpyDeviceToHost));
+    CK(read_small(h, out + done * row, h->obs + slot * row, run * row * 8));
     done += run;
   }
   h->obs_read += cnt;
@@ -417,8 +442,12 @@ int sw_get_spins(sw_handle* h, int8_t* dst, int is_device) {
   if (!h || !dst) return fail(SW_ERR_ARG, "sw_get_spins: bad arguments");
   int rc = check_device_status(h);
   if (rc) return rc;
-  CK(cudaMemcpy(dst, h->spins, (int64_t)h->L * h->L,
-                is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
+  if (is_device) {
+    CK(launch_copy_if(dst, h->spins, (int64_t)h->L * h->L, nullptr, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  } else {
+    CK(copy_on(h->stream, dst, h->spins, (size_t)h->L * h->L, cudaMemcpyDeviceToHost));
+  }
   return SW_OK;
 }
 
@@ -438,12 +467,10 @@ int sw_set_spins(sw_handle* h, const int8_t* src, int is_device) {
   }
   CK(cudaMemsetAsync(h->chk, 0, sizeof(int), h->stream));
   CK(launch_check_spins(dsrc, N, h->q, h->chk, h->stream));
+  CK(launch_copy_if(h->spins, dsrc, N, h->chk, h->stream));   // only if every value is valid
   int bad = 0;
-  CK(cudaMemcpyAsync(&bad, h->chk, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
+  CK(read_small(h, &bad, h->chk, sizeof(int)));
   if (bad) return fail(SW_ERR_ARG, "sw_set_spins: spin value outside [0, q)");
-  CK(cudaMemcpyAsync(h->spins, dsrc, N, cudaMemcpyDeviceToDevice, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
   return SW_OK;
 }
 
@@ -462,8 +489,8 @@ int sw_debug_dump(sw_handle* h, uint8_t* mask_out, int32_t* labels_out, int is_d
   }
   int rc = check_device_status(h);
   if (rc) return rc;
-  if (mask_out) CK(cudaMemcpy(mask_out, h->mask, (N + 3) / 4, kind));
-  if (labels_out) CK(cudaMemcpy(labels_out, h->labels, N * 4, kind));
+  if (mask_out) CK(copy_on(h->stream, mask_out, h->mask, (N + 3) / 4, kind));
+  if (labels_out) CK(copy_on(h->stream, labels_out, h->labels, N * 4, kind));
   return SW_OK;
 }
 

@@ -82,7 +82,8 @@ int batch_status(sw_batch* b) {
   cudaError_t e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return set_last_error(SW_ERR_CUDA, std::string("batch: ") + cudaGetErrorString(e));
   BatchCtl c;
-  e = cudaMemcpy(&c, b->ctl, sizeof(c), cudaMemcpyDeviceToHost);
+  e = cudaMemcpyAsync(&c, b->ctl, sizeof(c), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return set_last_error(SW_ERR_CUDA, std::string("batch: ") + cudaGetErrorString(e));
   if (c.err == SW_ERR_TIMEOUT)
     return set_last_error(SW_ERR_TIMEOUT, "batch: a grid barrier of the persistent sweep timed out");
@@ -279,7 +280,8 @@ int sw_batch_observables(sw_batch* b, int replica, int64_t* out, int max_sweeps,
   while (done < cnt) {
     const int64_t slot = (int64_t)((rd + done) % BATCH_OBS_CAP);
     const int64_t run = std::min<int64_t>(cnt - done, BATCH_OBS_CAP - slot);
-    e = cudaMemcpy(out + done * row, ring + slot * row, run * row * 8, cudaMemcpyDeviceToHost);
+    e = cudaMemcpyAsync(out + done * row, ring + slot * row, run * row * 8, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return set_last_error(SW_ERR_CUDA, std::string("sw_batch_observables: ") + cudaGetErrorString(e));
     done += run;
   }
@@ -292,8 +294,10 @@ int sw_batch_get_spins(sw_batch* b, int replica, int8_t* dst, int is_device) {
   if (!b || replica < 0 || replica >= b->n || !dst) return set_last_error(SW_ERR_ARG, "sw_batch_get_spins: bad arguments");
   int rc = batch_status(b);
   if (rc) return rc;
-  cudaError_t e = cudaMemcpy(dst, b->reps[replica].spins, (int64_t)b->L[replica] * b->L[replica],
-                             is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
+  const int64_t n = (int64_t)b->L[replica] * b->L[replica];
+  cudaError_t e = is_device ? launch_copy_if(dst, b->reps[replica].spins, n, nullptr, b->stream)
+                            : cudaMemcpyAsync(dst, b->reps[replica].spins, n, cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return set_last_error(SW_ERR_CUDA, std::string("sw_batch_get_spins: ") + cudaGetErrorString(e));
   return SW_OK;
 }

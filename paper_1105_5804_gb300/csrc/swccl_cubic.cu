@@ -39,6 +39,7 @@ struct sw3_handle {
   uint32_t* edge_words = nullptr; // edge-root bits of every brick
   int32_t* scratch = nullptr;     // labeling scratch of every brick
   SwCtl* ctl = nullptr;
+  int* chk = nullptr;             // spin-check flag of sw3_set_spins
   int64_t* obs = nullptr;
   uint64_t sweeps = 0, obs_read = 0;
   cudaGraph_t graph = nullptr;
@@ -65,6 +66,7 @@ void free3(sw3_handle* h) {
   cudaFree(h->edge_words);
   cudaFree(h->scratch);
   cudaFree(h->ctl);
+  cudaFree(h->chk);
   cudaFree(h->obs);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
@@ -78,10 +80,16 @@ cudaError_t finish3(sw3_handle* h) {
   return launch_observe3(h->spins, h->box, h->q, h->ctl, h->obs, OBS3_CAP, h->stream);
 }
 
+// Synchronous copy ordered on the handle's stream (not the legacy default stream).
+cudaError_t copy3(cudaStream_t st, void* dst, const void* src, size_t bytes, cudaMemcpyKind kind) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, kind, st);
+  return e != cudaSuccess ? e : cudaStreamSynchronize(st);
+}
+
 int status3(sw3_handle* h) {
   CK3(cudaStreamSynchronize(h->stream));
   SwCtl c;
-  CK3(cudaMemcpy(&c, h->ctl, sizeof(c), cudaMemcpyDeviceToHost));
+  CK3(copy3(h->stream, &c, h->ctl, sizeof(c), cudaMemcpyDeviceToHost));
   if (c.err) return fail3(c.err, "a device-side consistency check failed in a 3D sweep");
   return SW_OK;
 }
@@ -121,7 +129,7 @@ sw3_handle* sw3_create(int X, int Y, int Z, int q, uint64_t T, uint64_t seed, in
       cudaMalloc(&h->lroot, (size_t)n * 2) != cudaSuccess ||
       cudaMalloc(&h->edge_words, (size_t)edge_words3(h->box) * 4) != cudaSuccess ||
       cudaMalloc(&h->scratch, (size_t)scratch_ints3(h->box) * 4) != cudaSuccess ||
-      cudaMalloc(&h->ctl, sizeof(SwCtl)) != cudaSuccess ||
+      cudaMalloc(&h->ctl, sizeof(SwCtl)) != cudaSuccess || cudaMalloc(&h->chk, sizeof(int)) != cudaSuccess ||
       cudaMalloc(&h->obs, (size_t)OBS3_CAP * (q + 1) * 8) != cudaSuccess) {
     cudaGetLastError();
     return bail(SW_ERR_OOM, "sw3_create: cudaMalloc failed");
@@ -212,7 +220,7 @@ int sw3_observables(sw3_handle* h, int64_t* out, int max_sweeps, int* n_written)
   while (done < cnt) {
     const int64_t slot = (int64_t)((h->obs_read + done) % OBS3_CAP);
     const int64_t run = std::min<int64_t>(cnt - done, OBS3_CAP - slot);
-    CK3(cudaMemcpy(out + done * row, h->obs + slot * row, run * row * 8, cudaMemcpyDeviceToHost));
+    CK3(copy3(h->stream, out + done * row, h->obs + slot * row, run * row * 8, cudaMemcpyDeviceToHost));
     done += run;
   }
   h->obs_read += cnt;
@@ -224,7 +232,12 @@ int sw3_get_spins(sw3_handle* h, int8_t* dst, int is_device) {
   if (!h || !dst) return fail3(SW_ERR_ARG, "sw3_get_spins: bad arguments");
   int rc = status3(h);
   if (rc) return rc;
-  CK3(cudaMemcpy(dst, h->spins, (size_t)h->box.n(), is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
+  if (is_device) {
+    CK3(launch_copy_if(dst, h->spins, h->box.n(), nullptr, h->stream));
+    CK3(cudaStreamSynchronize(h->stream));
+  } else {
+    CK3(copy3(h->stream, dst, h->spins, (size_t)h->box.n(), cudaMemcpyDeviceToHost));
+  }
   return SW_OK;
 }
 
@@ -243,18 +256,12 @@ int sw3_set_spins(sw3_handle* h, const int8_t* src, int is_device) {
     dsrc = staging;
     h->labels_valid = false;
   }
-  int* flag = nullptr;
-  CK3(cudaMalloc(&flag, sizeof(int)));
-  cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), h->stream);
-  if (e == cudaSuccess) e = launch_check_spins(dsrc, n, h->q, flag, h->stream);
+  CK3(cudaMemsetAsync(h->chk, 0, sizeof(int), h->stream));
+  CK3(launch_check_spins(dsrc, n, h->q, h->chk, h->stream));
+  CK3(launch_copy_if(h->spins, dsrc, n, h->chk, h->stream));   // only if every value is valid
   int bad = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  cudaFree(flag);
-  if (e != cudaSuccess) return cuda_fail3(e, "sw3_set_spins: check");
+  CK3(copy3(h->stream, &bad, h->chk, sizeof(int), cudaMemcpyDeviceToHost));
   if (bad) return fail3(SW_ERR_ARG, "sw3_set_spins: a spin is outside [0, q)");
-  CK3(cudaMemcpyAsync(h->spins, dsrc, (size_t)n, cudaMemcpyDeviceToDevice, h->stream));
-  CK3(cudaStreamSynchronize(h->stream));
   return SW_OK;
 }
 

@@ -147,6 +147,8 @@ cudaError_t launch_pixel_bonds(const uint8_t* px, uint8_t* mask, int H, int W, i
                                cudaStream_t st);
 cudaError_t launch_philox_probe(long long calls_per_thread, int blocks, uint32_t* sink, cudaStream_t st);
 cudaError_t launch_check_spins(const int8_t* spins, int64_t n, int q, int* err, cudaStream_t st);
+// dst = src (device memory) if ok_flag is null or *ok_flag == 0; an SM copy.
+cudaError_t launch_copy_if(int8_t* dst, const int8_t* src, int64_t n, const int* ok_flag, cudaStream_t st);
 cudaError_t launch_init_spins_n(int8_t* spins, int64_t n, int q, uint64_t seed, int hot, cudaStream_t st);
 // Simple-cubic sweep (k_cubic.cu).  ev, if not null, receives five events:
 // before the local step, merge, flip, advance, and after the advance.  The
