@@ -173,6 +173,50 @@ def oracle_sample(seconds=15.0, L=4096):
             "cpu": _cpu_model(), "host_cores": os.cpu_count()}
 
 
+def _oracle_replica(args):
+    """One process of the all-cores baseline: serial oracle sweeps of an
+    independent L x L replica (seed 7 + r) for about `seconds`."""
+    r, L, seconds = args
+    sys.path.insert(0, ROOT)
+    import oracle
+    T = oracle.threshold(oracle.coupling_K(Q_BENCH, KC_ISING, 1.0, oracle.CONV_ISING))
+    s = oracle.init_spins(L, Q_BENCH, SEED_BENCH + r, True)
+    t0 = time.perf_counter()
+    n = 0
+    while time.perf_counter() - t0 < seconds:
+        s, _ = oracle.chain(L, Q_BENCH, T, SEED_BENCH + r, n, 1, s)
+        n += 1
+    return L * L * n, time.perf_counter() - t0
+
+
+def oracle_all_cores(seconds=8.0, L=1024):
+    """The oracle on every host core at once: one independent replica per
+    process (processes started with spawn: CUDA is already initialised)."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_replica, [(r, L, seconds) for r in range(cores)])
+    sites = sum(a for a, _ in res)
+    dt = max(b for _, b in res)
+    return {"value": sites / (dt * 1e9), "unit": "site-updates/ns", "cores": cores,
+            "sample": "%d independent oracle replicas of the L=%d q=2 Ising lattice at beta_c, one per core, "
+                      "%.1f s" % (cores, L, dt)}
+
+
+def oracle_ccl_sample(n_seeds=2, H=4096):
+    """The oracle's labeling (breadth-first search) of 4096^2 critical
+    percolation masks on one core."""
+    import oracle
+    masks = [oracle.perc_mask(H, H, k) for k in range(n_seeds)]
+    t0 = time.perf_counter()
+    for m in masks:
+        oracle.label(m, H, H, True)
+    dt = time.perf_counter() - t0
+    return {"value": H * H * n_seeds / (dt * 1e9), "unit": "Gsites/s", "cores": 1,
+            "sample": "oracle labeling of %d periodic %dx%d p=1/2 masks (seeds 0..%d), %.1f s"
+                      % (n_seeds, H, H, n_seeds - 1, dt)}
+
+
 def _cpu_model():
     try:
         with open("/proc/cpuinfo") as f:
@@ -624,6 +668,8 @@ def run_ours(args):
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(args.cpu_seconds)
+        line["cpu_baseline"]["all_cores"] = oracle_all_cores()
+        line["cpu_baseline"]["ccl"] = oracle_ccl_sample()
     print(json.dumps(line), flush=True)
 
 
