@@ -169,17 +169,53 @@ __device__ __forceinline__ void final_labels_tile(int32_t* labels, const Grid& g
   const int h = min(TILE_H, g.H - y0), w = min(TILE_W, g.W - x0);
   const int n = __ldcg(s.root_counts + t);
   const int32_t* list = s.roots + (int64_t)t * TILE_SITES;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    const int r = __ldcg(list + k);   // local index
-    table[r] = g_find(labels, tile_global(r, y0, x0, g.W), limit, s.err);
+  // 1. cluster roots of the tile roots, four walks of a thread in flight together
+  constexpr int U = 4;
+  for (int k0 = threadIdx.x; k0 < n; k0 += U * (int)blockDim.x) {
+    int r[U], x[U];
+    bool act[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int k = k0 + u * (int)blockDim.x;
+      act[u] = k < n;
+      r[u] = act[u] ? __ldcg(list + k) : 0;   // local index
+      x[u] = tile_global(r[u], y0, x0, g.W);
+    }
+    g_find_multi<U>(labels, x, act, limit, s.err);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (act[u]) table[r[u]] = x[u];
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < TILE_SITES; k += blockDim.x) {
-    const int ly = k >> TILE_W_LOG2, lx = k & (TILE_W - 1);
-    if (ly < h && lx < w) {
+  // 2. every site takes its tile root's cluster root: four sites per 16-byte
+  //    word when rows start 16-byte aligned (a 16-byte aligned array and
+  //    W % 4 == 0; x0 is a multiple of 256)
+  if ((g.W & 3) == 0 && (reinterpret_cast<uintptr_t>(labels) & 15) == 0) {
+    for (int k = threadIdx.x; k < TILE_SITES / 4; k += blockDim.x) {
+      const int sidx = 4 * k;
+      const int ly = sidx >> TILE_W_LOG2, lx = sidx & (TILE_W - 1);
+      if (ly >= h || lx >= w) continue;
       int32_t* p = labels + (int64_t)(y0 + ly) * g.W + x0 + lx;
-      const int v = __ldcg(p);
-      *p = table[v < 0 ? -v - 1 : k];
+      if (lx + 4 <= w) {
+        const int4 v = __ldcg(reinterpret_cast<const int4*>(p));
+        const int4 o = make_int4(table[v.x < 0 ? -v.x - 1 : sidx], table[v.y < 0 ? -v.y - 1 : sidx + 1],
+                                 table[v.z < 0 ? -v.z - 1 : sidx + 2], table[v.w < 0 ? -v.w - 1 : sidx + 3]);
+        *reinterpret_cast<int4*>(p) = o;
+      } else {
+        for (int j = 0; lx + j < w; ++j) {
+          const int v = __ldcg(p + j);
+          p[j] = table[v < 0 ? -v - 1 : sidx + j];
+        }
+      }
+    }
+  } else {
+    for (int k = threadIdx.x; k < TILE_SITES; k += blockDim.x) {
+      const int ly = k >> TILE_W_LOG2, lx = k & (TILE_W - 1);
+      if (ly < h && lx < w) {
+        int32_t* p = labels + (int64_t)(y0 + ly) * g.W + x0 + lx;
+        const int v = __ldcg(p);
+        *p = table[v < 0 ? -v - 1 : k];
+      }
     }
   }
   __syncthreads();

@@ -139,6 +139,36 @@ __device__ __forceinline__ int g_find(int* lab, int x, int limit, int* err) {
   return x;
 }
 
+// g_find of up to U nodes at once (those with act[u] set): the walks run in
+// lock step so that their loads are in flight together.  x[u] is replaced by
+// its root; same path halving and step limit as g_find.
+template <int U>
+__device__ __forceinline__ void g_find_multi(int* lab, int (&x)[U], const bool (&act)[U], int limit, int* err) {
+  int p[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) p[u] = act[u] ? g_load(lab + x[u]) : x[u];
+  for (int steps = 0;; ++steps) {
+    int gp[U];
+    bool more = false;
+#pragma unroll
+    for (int u = 0; u < U; ++u) gp[u] = (p[u] != x[u]) ? g_load(lab + p[u]) : p[u];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (p[u] != x[u]) {
+        if (gp[u] != p[u]) atomicMin(lab + x[u], gp[u]);
+        x[u] = p[u];
+        p[u] = gp[u];
+        more = true;
+      }
+    }
+    if (!more) return;
+    if (steps > limit) {
+      set_error(err, SW_ERR_STATE);
+      return;
+    }
+  }
+}
+
 __device__ __forceinline__ void g_union(int* lab, int a, int b, int limit, int* err) {
   for (int rounds = 0; rounds <= limit; ++rounds) {
     a = g_find(lab, a, limit, err);
