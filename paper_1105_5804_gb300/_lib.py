@@ -168,6 +168,7 @@ def sw_create_threshold(L, q, T, seed, hot_start, stream=0):
 
 
 def sw_destroy(h):
+    _shape.pop(h, None)
     _check(lib().sw_destroy(h))
 
 
@@ -186,8 +187,19 @@ def sw_get_info(h):
     return {k: int(v) for k, v in zip(keys, info)}
 
 
+_shape = {}   # handle -> (L, q): fixed for a handle's life, dropped by sw_destroy
+
+
+def _Lq(h):
+    v = _shape.get(h)
+    if v is None:
+        i = sw_get_info(h)
+        v = _shape[h] = (i["L"], i["q"])
+    return v
+
+
 def sw_observables(h, max_sweeps=4096):
-    q = sw_get_info(h)["q"]
+    q = _Lq(h)[1]
     out = np.zeros((max_sweeps, 1 + q), dtype=np.int64)
     n = ctypes.c_int(0)
     _check(lib().sw_observables(h, out.ctypes.data, max_sweeps, ctypes.byref(n)))
@@ -197,8 +209,7 @@ def sw_observables(h, max_sweeps=4096):
 def sw_get_spins(h, out=None):
     """Current spins: into ``out`` (a host numpy int8 array or a CUDA int8
     tensor) or into a new numpy array."""
-    info = sw_get_info(h)
-    N = info["L"] ** 2
+    N = _Lq(h)[0] ** 2
     if out is None or isinstance(out, np.ndarray):
         a = np.empty(N, dtype=np.int8) if out is None else out
         if a.dtype != np.int8 or a.size < N or not a.flags["C_CONTIGUOUS"]:
@@ -212,7 +223,7 @@ def sw_get_spins(h, out=None):
 
 def sw_set_spins(h, src):
     import torch
-    N = sw_get_info(h)["L"] ** 2
+    N = _Lq(h)[0] ** 2
     if isinstance(src, torch.Tensor) and src.is_cuda:
         _check(lib().sw_set_spins(h, _dev(src, torch.int8, N, "src"), 1))
     else:
@@ -225,7 +236,7 @@ def sw_set_spins(h, src):
 def sw_debug_dump(h, mask_out=None, labels_out=None):
     """(mask, labels) of the last sweep, as numpy arrays, or into CUDA tensors."""
     import torch
-    N = sw_get_info(h)["L"] ** 2
+    N = _Lq(h)[0] ** 2
     if mask_out is None and labels_out is None:
         m = np.empty(mask_bytes(N), dtype=np.uint8)
         lab = np.empty(N, dtype=np.int32)
