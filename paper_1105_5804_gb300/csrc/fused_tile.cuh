@@ -20,21 +20,10 @@ __device__ __forceinline__ uint32_t eq4(uint32_t a, uint32_t b) {
   return (z * 0x00204081u) >> 21 & 0xFu;
 }
 
-// Spread the 32 bits of v to the even bits of a 64-bit word.
-__device__ __forceinline__ unsigned long long spread_even(uint32_t v) {
-  unsigned long long x = v;
-  x = (x | (x << 16)) & 0x0000FFFF0000FFFFull;
-  x = (x | (x << 8)) & 0x00FF00FF00FF00FFull;
-  x = (x | (x << 4)) & 0x0F0F0F0F0F0F0F0Full;
-  x = (x | (x << 2)) & 0x3333333333333333ull;
-  x = (x | (x << 1)) & 0x5555555555555555ull;
-  return x;
-}
-
 // Bonds of 32 consecutive sites of one row, and the observables of the
 // spins read (bonds joining equal spins; sites per state for q <= QREG).
 struct RowBonds {
-  unsigned long long word;  // bit 2i east bond, 2i+1 north bond (rule of Eq. 7)
+  uint32_t east, north;     // bit i: east / north bond of site i (rule of Eq. 7)
   int n_eq;                 // equal east and north neighbours among the sites
   int cnt[8];               // sites per state (q <= 8)
 };
@@ -94,24 +83,25 @@ __device__ __forceinline__ void row_bonds(const int8_t* __restrict__ spins, int 
       rb.cnt[c] = m;
     }
   }
-  // bonds: site i's east bit at 2i, north bit at 2i+1; one Philox call per pair
-  const unsigned long long eqw = spread_even(eq_e) | (spread_even(eq_n) << 1);
+  // bonds: one Philox call per pair of sites i, i+1 (words: east i, north i,
+  // east i+1, north i+1)
   if (T >= (1ull << 32)) {
-    rb.word = eqw;                       // p = 1: every bond between equal spins opens
+    rb.east = eq_e;                      // p = 1: every bond between equal spins opens
+    rb.north = eq_n;
   } else if (T == 0) {
-    rb.word = 0ull;
+    rb.east = rb.north = 0u;
   } else {
     const uint32_t thr = (uint32_t)T;
-    unsigned long long word = 0ull;
+    uint32_t e = 0u, n = 0u;
 #pragma unroll
     for (int i = 0; i < 32; i += 2) {
       if (i >= nvalid) break;
       const uint4 r = philox(make_uint4((uint32_t)((row + x + i) >> 1), sw_lo, sw_hi, TAG_BOND), klo, khi);
-      const uint32_t c = (uint32_t)(r.x < thr) | ((uint32_t)(r.y < thr) << 1) | ((uint32_t)(r.z < thr) << 2) |
-                         ((uint32_t)(r.w < thr) << 3);
-      word |= (unsigned long long)c << (2 * i);
+      e |= ((uint32_t)(r.x < thr) | ((uint32_t)(r.z < thr) << 1)) << i;
+      n |= ((uint32_t)(r.y < thr) | ((uint32_t)(r.w < thr) << 1)) << i;
     }
-    rb.word = word & eqw;
+    rb.east = e & eq_e;
+    rb.north = n & eq_n;
   }
 }
 
@@ -214,17 +204,18 @@ __device__ __forceinline__ void sw_label_tile(const SwRep& R, int t, uint64_t sw
   {
     const int ly = lane, c = warp;
     const int nvalid = min(max(w - 32 * c, 0), 32);
-    unsigned long long wd = 0ull;
+    uint32_t we = 0u, wn = 0u;
     if (ly < h && nvalid > 0) {
       const int y = y0 + ly, x = x0 + 32 * c;
       RowBonds rb;
       row_bonds(spins, L, y, x, nvalid, T, (uint32_t)seed, (uint32_t)(seed >> 32), (uint32_t)sweep,
                 (uint32_t)(sweep >> 32), q, rb);
-      wd = rb.word;
+      we = rb.east;
+      wn = rb.north;
       if (32 * c + nvalid == w) {                 // east bond leaving the tile
-        const int bit = 2 * (nvalid - 1);
-        if ((wd >> bit) & 1ull) atomicOr(&e_last, 1u << ly);
-        wd &= ~(1ull << bit);
+        const uint32_t bit = 1u << (nvalid - 1);
+        if (we & bit) atomicOr(&e_last, 1u << ly);
+        we &= ~bit;
       }
       if (do_obs) {
         n_eq = rb.n_eq;
@@ -237,7 +228,8 @@ __device__ __forceinline__ void sw_label_tile(const SwRep& R, int t, uint64_t sw
         }
       }
     }
-    sm.mb[ly * STRIPS + c] = wd;
+    sm.be[ly * STRIPS + c] = we;
+    sm.bn[ly * STRIPS + c] = wn;
   }
   __syncthreads();
 
@@ -295,7 +287,7 @@ __device__ __forceinline__ void sw_label_tile(const SwRep& R, int t, uint64_t sw
     const bool ok = k < w;
     rec[SeamLayout::ROW_B + k] = edge_root(ok, ok ? root_at(0, k) : 0);
     rec[SeamLayout::ROW_T + k] = edge_root(ok, ok ? root_at(h - 1, k) : 0);
-    const bool n = ok && ((sm.mb[(h - 1) * STRIPS + (k >> 5)] >> (2 * (k & 31) + 1)) & 1ull);
+    const bool n = ok && ((sm.bn[(h - 1) * STRIPS + (k >> 5)] >> (k & 31)) & 1u);
     const uint32_t nb = __ballot_sync(FULL, n);
     if (lane == 0) rec[SeamLayout::N_BITS + (k >> 5)] = (int32_t)nb;
   }

@@ -211,7 +211,8 @@ k3_local(const int8_t* __restrict__ spins, uint16_t* __restrict__ lroot, int32_t
     const uint32_t xw = __ballot_sync(FULL, o0 && lx + 1 == k.w && b.bx == 1);
     const uint32_t zw = __ballot_sync(FULL, o2 && lz + 1 == k.d && b.bz == 1);
     if (lane == 0) {
-      sm.mb[lz * STRIPS + ly] = spread_even(east) | (spread_even(north) << 1);
+      sm.be[lz * STRIPS + ly] = east;
+      sm.bn[lz * STRIPS + ly] = north;
       ls.ybits[lz * B3Y + ly] = ybit;
       ls.xwrap[lz * B3Y + ly] = xw;
       if (zw) ls.zwrap[ly] = zw;

@@ -8,6 +8,17 @@
 
 namespace swccl {
 
+// The even bits of a 64-bit word, packed into 32 bits (bit 2i -> bit i).
+__device__ __forceinline__ uint32_t even_bits(unsigned long long x) {
+  x &= 0x5555555555555555ull;
+  x = (x | (x >> 1)) & 0x3333333333333333ull;
+  x = (x | (x >> 2)) & 0x0F0F0F0F0F0F0F0Full;
+  x = (x | (x >> 4)) & 0x00FF00FF00FF00FFull;
+  x = (x | (x >> 8)) & 0x0000FFFF0000FFFFull;
+  x = (x | (x >> 16)) & 0x00000000FFFFFFFFull;
+  return (uint32_t)x;
+}
+
 // Local labeling of one tile for the stand-alone labeling path: the tile's
 // bond bits are copied from the packed mask into shared memory (bits of
 // sites outside the grid and the east bond of the tile's last column
@@ -24,7 +35,6 @@ template <bool LOCAL = false>
 __device__ __forceinline__ void ccl_label_tile(const uint8_t* __restrict__ mask, int32_t* __restrict__ labels,
                                                const Grid& g, const LabelScratch& s, int t, TileSmem& sm) {
   int* par = sm.par;
-  unsigned long long* mb = sm.mb;
   int* warp_roots = sm.warp_roots;
 
   const int ty = t / g.tiles_x, tx = t - ty * g.tiles_x;
@@ -51,7 +61,8 @@ __device__ __forceinline__ void ccl_label_tile(const uint8_t* __restrict__ mask,
       if (nvalid < 32) wd &= (1ull << (2 * nvalid)) - 1ull;
       if (32 * c + nvalid == w) wd &= ~(1ull << (2 * (nvalid - 1)));   // east bond leaving the tile
     }
-    mb[k] = wd;
+    sm.be[k] = even_bits(wd);        // the mask interleaves east (even) and north (odd) bits
+    sm.bn[k] = even_bits(wd >> 1);
   }
   __syncthreads();
 
@@ -114,7 +125,7 @@ __device__ __forceinline__ void ccl_label_tile(const uint8_t* __restrict__ mask,
     const bool ok = k < w;
     rec[SeamLayout::ROW_B + k] = ok ? glabel(0, k) : -1;
     rec[SeamLayout::ROW_T + k] = ok ? glabel(h - 1, k) : -1;
-    const bool n = ok && ((mb[(h - 1) * STRIPS + (k >> 5)] >> (2 * (k & 31) + 1)) & 1ull);
+    const bool n = ok && ((sm.bn[(h - 1) * STRIPS + (k >> 5)] >> (k & 31)) & 1u);
     const uint32_t nb = __ballot_sync(FULL, n);
     if (lane == 0) rec[SeamLayout::N_BITS + (k >> 5)] = (int32_t)nb;
   }

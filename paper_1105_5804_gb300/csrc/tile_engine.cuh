@@ -2,16 +2,18 @@
 // stand-alone labeling kernel (bond mask in memory) and the fused
 // Swendsen-Wang kernel (bonds drawn on the fly).
 //
-// Input: the tile's bond bits in shared memory, one 64-bit word per row and
-// 32-column strip (bit 2i: east bond of site i, bit 2i+1: north bond), with
-// bits of sites outside the grid and the east bond of the tile's last column
-// cleared.  Output: par[] such that every site's tile root is
-// par[par[site]], the root being the smallest local index of the site's
-// tile component.
+// Input: the tile's bond bits in shared memory, two 32-bit words per row and
+// 32-column strip (be: bit i = east bond of site i of the strip; bn: bit i =
+// its north bond), with bits of sites outside the grid and the east bond of
+// the tile's last column cleared.  A row's words are the lane masks the sweep
+// needs, so it reads them with one broadcast load each.  Output: par[] such
+// that every site's tile root is par[par[site]], the root being the smallest
+// local index of the site's tile component.
 //
 //  1. warp c sweeps strip c from row 0 upwards with the labels of the row
-//     below in registers.  A row is cut into runs of east-joined sites with
-//     one ballot.  A run reached from below through north bonds takes the
+//     below in registers.  A row is cut into runs of east-joined sites by bit
+//     operations on its east word.  A run reached from below (the north word
+//     of the row below) takes the
 //     label of its leftmost such site (one shuffle); a run nothing reaches
 //     gets a fresh label, the index of its first site (a union-find node).
 //     A lane reached from below by a label other than its run's appends the
@@ -40,7 +42,8 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 
 struct TileSmem {
   alignas(16) int par[TILE_SITES];   // 16-byte aligned: read as int4 when the tile roots are written
-  unsigned long long mb[TILE_H * STRIPS];
+  uint32_t be[TILE_H * STRIPS];   // east bonds, bit = lane of the strip
+  uint32_t bn[TILE_H * STRIPS];   // north bonds
   int warp_count[STRIPS];
   int warp_roots[LABEL_THREADS / 32];
   int n_hooked;
@@ -51,7 +54,7 @@ __device__ __forceinline__ int tile_global(int r, int y0, int x0, int W) {
   return (y0 + (r >> TILE_W_LOG2)) * W + x0 + (r & (TILE_W - 1));
 }
 
-// Runs the engine; sm.mb must be filled and sm.n_hooked zero, followed by a
+// Runs the engine; sm.be and sm.bn must be filled and sm.n_hooked zero, followed by a
 // __syncthreads().  `slot` (TILE_SITES ints of global scratch) holds the
 // pair lists; `hook_log` (TILE_SITES ints) the hooked roots.  Ends with a
 // __syncthreads().
@@ -59,7 +62,8 @@ __device__ __forceinline__ void tile_engine(TileSmem& sm, int h, int w, int32_t*
                                             int* err) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int* par = sm.par;
-  unsigned long long* mb = sm.mb;
+  const uint32_t* be = sm.be;
+  const uint32_t* bn = sm.bn;
   int* warp_count = sm.warp_count;
   // 1. strip sweep
   {
@@ -68,11 +72,11 @@ __device__ __forceinline__ void tile_engine(TileSmem& sm, int h, int w, int32_t*
     int32_t* pairs = slot + warp * PAIR_CAP;
     int n_pairs = 0;
     int lab_below = 0;
-    bool up_open = false;       // north bond from the site below into this lane's site
+    uint32_t upb = 0u;          // north bonds of the row below: the lanes reached from below
     for (int ly = 0; ly < h; ++ly) {
-      const uint32_t b = (uint32_t)(mb[ly * STRIPS + warp] >> (2 * lane)) & 3u;
-      const uint32_t east = __ballot_sync(FULL, b & 1u) & 0x7FFFFFFFu;   // runs stay inside the strip
-      const uint32_t upb = __ballot_sync(FULL, up_open);
+      const uint32_t east = be[ly * STRIPS + warp] & 0x7FFFFFFFu;   // runs stay inside the strip
+      const uint32_t nrow = bn[ly * STRIPS + warp];
+      const bool up_open = (upb >> lane) & 1u;   // north bond from the site below into this lane's site
       const uint32_t breaks = ~east & below_lanes;
       const int start = breaks ? 32 - __clz(breaks) : 0;
       const int end = lane + __ffs(~east >> lane) - 1;
@@ -89,7 +93,7 @@ __device__ __forceinline__ void tile_engine(TileSmem& sm, int h, int w, int32_t*
       if (pair) pairs[n_pairs + __popc(pm & below_lanes)] = (lab_below << 16) | label;
       n_pairs += __popc(pm);
       lab_below = label;
-      up_open = (b & 2u) != 0;
+      upb = nrow;
     }
     if (lane == 0) warp_count[warp] = n_pairs;
   }
@@ -106,10 +110,10 @@ __device__ __forceinline__ void tile_engine(TileSmem& sm, int h, int w, int32_t*
       if (k < SEAMS) {
         const int ly = k / (STRIPS - 1), c = k - ly * (STRIPS - 1);
         if (ly >= h) continue;
-        if (!((mb[ly * STRIPS + c] >> 62) & 1ull)) continue;
+        if (!((be[ly * STRIPS + c] >> 31) & 1u)) continue;
         if (ly > 0) {
-          const unsigned long long lo = mb[(ly - 1) * STRIPS + c], hi = mb[(ly - 1) * STRIPS + c + 1];
-          if (((lo >> 62) & 1ull) && ((lo >> 63) & 1ull) && ((hi >> 1) & 1ull)) continue;   // joined below
+          const int k0 = (ly - 1) * STRIPS + c;
+          if (((be[k0] >> 31) & 1u) && ((bn[k0] >> 31) & 1u) && (bn[k0 + 1] & 1u)) continue;   // joined below
         }
         a = ly * TILE_W + c * 32 + 31;
         b = a + 1;
