@@ -245,13 +245,56 @@ def test_fused_many_states(q):
 
 
 @pytest.mark.parametrize("T", [0, 1, 1 << 31, (1 << 32) - 1, 1 << 32])
-def test_fused_degenerate_thresholds(T):
-    _run_fused(68, 2, T, seed=3, hot=True, n_sweeps=4)
+@pytest.mark.parametrize("per_call", [1, 4])
+def test_fused_degenerate_thresholds(T, per_call):
+    _run_fused(68, 2, T, seed=3, hot=True, n_sweeps=8, per_call=per_call)
 
 
 def test_fused_timed_mode_and_one_sweep_per_call():
     T = oracle.threshold(oracle.coupling_K(2, KC, 1.0, oracle.CONV_ISING))
     _run_fused(292, 2, T, seed=12, hot=True, n_sweeps=6, timing=True)
+
+
+def test_fused_timed_mode_several_sweeps_per_call():
+    T = oracle.threshold(oracle.coupling_K(3, math.log(1 + math.sqrt(3)), 1.0, oracle.CONV_POTTS))
+    h = sw.sw_create_threshold(292, 3, T, 21, True)
+    try:
+        sw.sw_set_timing(h, True)
+        s = oracle.init_spins(292, 3, 21, True)
+        done = 0
+        for k in (3, 2, 5):
+            sw.sw_sweep(h, k)
+            s, obs = oracle.chain(292, 3, T, 21, done, k, s)
+            assert np.array_equal(sw.sw_get_spins(h), s), done
+            assert np.array_equal(sw.sw_observables(h, 4096), obs), done
+            done += k
+        ms, n = sw.sw_phase_times(h)
+        assert n == done and all(v >= 0 for v in ms.values())
+    finally:
+        sw.sw_destroy(h)
+
+
+# Calls of 1 to 6 fused sweeps on lattices of one tile that is its own east
+# and north neighbour (L = 4, 8), ragged tiles (36, 260, 292) and several
+# ragged tiles each way (516); q = 127 counts the states one by one.
+@pytest.mark.parametrize("L", [4, 8, 36, 260, 292, 516])
+@pytest.mark.parametrize("q", [2, 3, 127])
+def test_fused_calls_of_several_sweeps(L, q):
+    beta = math.log(1 + math.sqrt(q))
+    T = oracle.threshold(oracle.coupling_K(q, beta, 1.0, oracle.CONV_POTTS))
+    seed = 3000 + L + q
+    h = sw.sw_create_threshold(L, q, T, seed, True)
+    try:
+        s = oracle.init_spins(L, q, seed, True)
+        done = 0
+        for k in (2, 3, 6, 1, 4, 5):
+            sw.sw_sweep(h, k)
+            s, obs = oracle.chain(L, q, T, seed, done, k, s)
+            assert np.array_equal(sw.sw_get_spins(h), s), (L, q, done, k)
+            assert np.array_equal(sw.sw_observables(h, 4096), obs), (L, q, done, k)
+            done += k
+    finally:
+        sw.sw_destroy(h)
 
 
 def test_mode_switches_keep_the_chain():
@@ -292,25 +335,24 @@ def test_mode_switches_keep_the_chain():
 @pytest.mark.parametrize("q,beta,conv", [(2, KC, sw.SW_CONV_ISING), (4, math.log(3.0), sw.SW_CONV_POTTS)])
 def test_fused_L16384_one_step_equivalence(q, beta, conv):
     """The benchmark's lattice and mode: L = 16384, hot start seed 7, fused
-    sweeps.  Sweep 0 is checked in full against the oracle stepping the
-    initial spins; after two more fused sweeps, sweep 3 is checked from the
-    GPU's pre-sweep spins."""
+    sweeps.  Sweep 0 (one sweep per call) is checked in full against the
+    oracle stepping the initial spins; then one call of three sweeps (as the
+    benchmark calls them, many per call) is checked against the oracle's
+    chain from the GPU's spins after sweep 0."""
     L, seed = 16384, 7
     T = oracle.threshold(oracle.coupling_K(q, beta, 1.0, conv))
     h = sw.sw_create_ex(L, q, beta, 1.0, conv, seed, True)
     try:
         s = sw.sw_get_spins(h)
-        for k in (0, 3):
-            if k > 0:
-                sw.sw_sweep(h, k - 1)
-                sw.sw_observables(h, 4096)
-                s = sw.sw_get_spins(h)
-            sw.sw_sweep(h, 1)
-            gs = sw.sw_get_spins(h)
-            gobs = sw.sw_observables(h, 4)
-            s_new, _, _, obs = oracle.sweep(L, q, T, seed, k, s)
-            assert np.array_equal(gs, s_new)
-            assert np.array_equal(gobs[-1], obs)
-            s = gs
+        sw.sw_sweep(h, 1)
+        gs = sw.sw_get_spins(h)
+        gobs = sw.sw_observables(h, 4)
+        s_new, _, _, obs = oracle.sweep(L, q, T, seed, 0, s)
+        assert np.array_equal(gs, s_new)
+        assert np.array_equal(gobs[-1], obs)
+        sw.sw_sweep(h, 3)
+        s3, obs3 = oracle.chain(L, q, T, seed, 1, 3, gs)
+        assert np.array_equal(sw.sw_get_spins(h), s3)
+        assert np.array_equal(sw.sw_observables(h, 4), obs3)
     finally:
         sw.sw_destroy(h)
