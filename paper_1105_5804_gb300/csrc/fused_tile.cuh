@@ -352,17 +352,24 @@ __device__ __forceinline__ void flip_tile_core(const SwRep& R, int t, uint64_t s
   // the tile's edge-root bits, left by the labeling kernel
   fs.edge_bits[threadIdx.x] = (uint32_t)__ldcg(R.s.roots + (int64_t)t * TILE_SITES + threadIdx.x);
 
-  // 2. my roots
-  uint32_t mine = 0;   // bit 8j + i: site i of pass j is a root
+  // 2. my roots: a site is a tile root iff its entry is its own local index.
+  //    Word k of pass j holds sites 2k and 2k + 1; both are compared at once
+  //    (a half-word is zero iff its low 15 bits plus 0x7FFF stay below bit
+  //    15 and its bit 15 is clear).  Sites outside the tile hold 0xFFFF and
+  //    never match.  Bit 4j + k of `mine` flags site 2k of pass j, bit
+  //    16 + 4j + k site 2k + 1.
+  uint32_t mine = 0;
 #pragma unroll
   for (int j = 0; j < PASSES; ++j) {
-    const int ly = 8 * j + warp;
     const uint4 rv = roots.get(j);
+    const uint32_t base = (uint32_t)((8 * j + warp) * TILE_W + lx0);
+    const uint32_t own = base * 0x00010001u + 0x00010000u;   // (base, base + 1)
+    const uint32_t wv[4] = {rv.x, rv.y, rv.z, rv.w};
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int lx = lx0 + i;
-      if (ly >= h || lx >= w) continue;
-      if (root_in(rv, i) == ly * TILE_W + lx) mine |= 1u << (8 * j + i);
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t x = wv[k] ^ (own + (uint32_t)k * 0x00020002u);
+      const uint32_t nz = ((x & 0x7FFF7FFFu) + 0x7FFF7FFFu) | x;
+      mine |= (~nz & 0x80008000u) >> (15 - (4 * j + k));
     }
   }
   const int cnt = __popc(mine);
@@ -384,7 +391,8 @@ __device__ __forceinline__ void flip_tile_core(const SwRep& R, int t, uint64_t s
   while (mine) {   // the tile's root list, edge roots flagged
     const int b = __ffs(mine) - 1;
     mine &= mine - 1;
-    const int r = (8 * (b >> 3) + warp) * TILE_W + lx0 + (b & 7);
+    const int jk = b & 15;
+    const int r = (8 * (jk >> 2) + warp) * TILE_W + lx0 + 2 * (jk & 3) + (b >> 4);
     rlist[base++] = (uint16_t)r | (((fs.edge_bits[r >> 5] >> (r & 31)) & 1u) ? EDGE_ROOT : (uint16_t)0);
   }
   __syncthreads();
