@@ -169,10 +169,15 @@ __device__ __forceinline__ void g_find_multi(int* lab, int (&x)[U], const bool (
   }
 }
 
+// The two finds of a round walk in lock step, so that their loads are in
+// flight together.
 __device__ __forceinline__ void g_union(int* lab, int a, int b, int limit, int* err) {
   for (int rounds = 0; rounds <= limit; ++rounds) {
-    a = g_find(lab, a, limit, err);
-    b = g_find(lab, b, limit, err);
+    int x[2] = {a, b};
+    const bool act[2] = {true, true};
+    g_find_multi<2>(lab, x, act, limit, err);
+    a = x[0];
+    b = x[1];
     if (a == b) return;
     if (a > b) { const int t = a; a = b; b = t; }
     const int old = atomicMin(lab + b, a);
