@@ -397,25 +397,40 @@ __device__ __forceinline__ void flip_tile_core(const SwRep& R, int t, uint64_t s
   }
   __syncthreads();
 
-  // 4. one draw per tile root, keyed by its cluster's final root
+  // 4. one draw per tile root, keyed by its cluster's final root; a thread
+  //    takes its roots two at a time, their parent walks in lock step
   const uint32_t klo = (uint32_t)seed, khi = (uint32_t)(seed >> 32);
-  for (int k = threadIdx.x; k < n_roots; k += LABEL_THREADS) {
-    const int raw = rlist[k];
-    const int r = raw & ROOT_MASK;
-    int Rg = tile_global(r, y0, x0, L);
-    if (raw & EDGE_ROOT) Rg = g_find(gpar, Rg, limit, err);
-    if (FEW) {
-      // the cluster's current state, read at the tile root (this tile's own
-      // site: step 5 rewrites it only after a barrier)
-      int v = spins[(int64_t)(y0 + (r >> TILE_W_LOG2)) * L + x0 + (r & (TILE_W - 1))];
-      if ((__ldcg(sel + (Rg >> 5)) >> (Rg & 31)) & 1u) {
-        const uint4 d = philox(make_uint4((uint32_t)Rg, (uint32_t)sweep, (uint32_t)(sweep >> 32), TAG_FLIP), klo, khi);
-        if ((uint64_t)d.y < P) v = (v + 1 + state_of(d.x, q - 1)) % q;
+  constexpr int U = 2;
+  for (int k0 = threadIdx.x; k0 < n_roots; k0 += U * LABEL_THREADS) {
+    int r[U], Rg[U];
+    bool act[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int k = k0 + u * LABEL_THREADS;
+      const int raw = k < n_roots ? (int)rlist[k] : 0;
+      r[u] = raw & ROOT_MASK;
+      Rg[u] = tile_global(r[u], y0, x0, L);
+      act[u] = k < n_roots && (raw & EDGE_ROOT);
+    }
+    g_find_multi<U>(gpar, Rg, act, limit, err);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (k0 + u * LABEL_THREADS >= n_roots) break;
+      if (FEW) {
+        // the cluster's current state, read at the tile root (this tile's own
+        // site: step 5 rewrites it only after a barrier)
+        int v = spins[(int64_t)(y0 + (r[u] >> TILE_W_LOG2)) * L + x0 + (r[u] & (TILE_W - 1))];
+        if ((__ldcg(sel + (Rg[u] >> 5)) >> (Rg[u] & 31)) & 1u) {
+          const uint4 d =
+              philox(make_uint4((uint32_t)Rg[u], (uint32_t)sweep, (uint32_t)(sweep >> 32), TAG_FLIP), klo, khi);
+          if ((uint64_t)d.y < P) v = (v + 1 + state_of(d.x, q - 1)) % q;
+        }
+        ns[r[u]] = (uint8_t)v;
+      } else {
+        const uint4 d =
+            philox(make_uint4((uint32_t)Rg[u], (uint32_t)sweep, (uint32_t)(sweep >> 32), TAG_FLIP), klo, khi);
+        ns[r[u]] = (uint8_t)state_of(d.x, q);
       }
-      ns[r] = (uint8_t)v;
-    } else {
-      const uint4 d = philox(make_uint4((uint32_t)Rg, (uint32_t)sweep, (uint32_t)(sweep >> 32), TAG_FLIP), klo, khi);
-      ns[r] = (uint8_t)state_of(d.x, q);
     }
   }
   __syncthreads();

@@ -78,6 +78,27 @@ __device__ __forceinline__ int sm_find(volatile int* par, int x, int limit, int*
   return x;
 }
 
+// sm_find of two nodes at once: the walks run in lock step, so that their
+// shared-memory loads overlap; same path halving and step limit.
+__device__ __forceinline__ void sm_find2(volatile int* par, int& a, int& b, int limit, int* err) {
+  int pa = par[a], pb = par[b];
+  for (int steps = 0; pa != a || pb != b; ++steps) {
+    const int ga = (pa != a) ? par[pa] : pa;
+    const int gb = (pb != b) ? par[pb] : pb;
+    if (pa != a) {
+      if (ga != pa) atomicMin((int*)&par[a], ga);
+      a = pa;
+      pa = ga;
+    }
+    if (pb != b) {
+      if (gb != pb) atomicMin((int*)&par[b], gb);
+      b = pb;
+      pb = gb;
+    }
+    if (steps > limit) { set_error(err, SW_ERR_STATE); return; }
+  }
+}
+
 // Join the sets of a and b.  atomicMin hooks the larger root under the
 // smaller; when the target was hooked meanwhile, the returned old parent is
 // joined in the next round, so no link is lost.  Every round strictly lowers
@@ -102,8 +123,7 @@ __device__ __forceinline__ void sm_union_log(int* par, int a, int b, int limit, 
                                              int* n_hooked, int cap) {
   volatile int* vp = par;
   for (int rounds = 0; rounds <= limit; ++rounds) {
-    a = sm_find(vp, a, limit, err);
-    b = sm_find(vp, b, limit, err);
+    sm_find2(vp, a, b, limit, err);
     if (a == b) return;
     if (a > b) { const int t = a; a = b; b = t; }
     const int old = atomicMin(&par[b], a);
