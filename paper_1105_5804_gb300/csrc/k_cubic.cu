@@ -366,12 +366,22 @@ k3_flip(int8_t* __restrict__ spins, const uint16_t* __restrict__ lroot, int32_t*
     rlist[base++] = (uint16_t)((lz * B3Y + ly) * B3X + lx);
   }
   __syncthreads();
-  // 3. one draw per brick root, keyed by its cluster's root
-  for (int j = threadIdx.x; j < n_roots; j += B3_THREADS) {
-    const int r = rlist[j];
-    int R = (int)brick_global(b, k, r);
-    if ((edge[r >> 5] >> (r & 31)) & 1u) R = g_find(gpar, R, limit, err);
-    ns[r] = (uint8_t)state_of(draw((uint32_t)R, sweep, TAG_FLIP, seed).x, q);
+  // 3. one draw per brick root, keyed by its cluster's root; a thread takes
+  //    its roots two at a time, their parent walks in lock step
+  for (int j0 = threadIdx.x; j0 < n_roots; j0 += 2 * B3_THREADS) {
+    int r[2], R[2];
+    bool act[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int j = j0 + u * B3_THREADS;
+      r[u] = j < n_roots ? (int)rlist[j] : 0;
+      R[u] = (int)brick_global(b, k, r[u]);
+      act[u] = j < n_roots && ((edge[r[u] >> 5] >> (r[u] & 31)) & 1u);
+    }
+    g_find_multi<2>(gpar, R, act, limit, err);
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+      if (j0 + u * B3_THREADS < n_roots) ns[r[u]] = (uint8_t)state_of(draw((uint32_t)R[u], sweep, TAG_FLIP, seed).x, q);
   }
   __syncthreads();
   // 4. every site takes its brick root's state
