@@ -18,9 +18,9 @@
 //     gets a fresh label, the index of its first site (a union-find node).
 //     A lane reached from below by a label other than its run's appends the
 //     pair to its warp's list: no union-find work happens inside the sweep;
-//  2. the east bonds between strips and all listed pairs are joined by all
-//     threads at once with the shared-memory union-find (larger root hooked
-//     under the smaller); hooked roots are logged;
+//  2. warp c joins the east bonds from strip c into strip c + 1 (one row per
+//     lane) and the pairs it listed, with the shared-memory union-find
+//     (larger root hooked under the smaller); hooked roots are logged;
 //  3. logged roots resolve their final roots, so every node points at its
 //     root and every site's label (a node) is one step from it.
 // The root is the smallest index of the tile component: the component's
@@ -44,7 +44,6 @@ struct TileSmem {
   alignas(16) int par[TILE_SITES];   // 16-byte aligned: read as int4 when the tile roots are written
   uint32_t be[TILE_H * STRIPS];   // east bonds, bit = lane of the strip
   uint32_t bn[TILE_H * STRIPS];   // north bonds
-  int warp_count[STRIPS];
   int warp_roots[LABEL_THREADS / 32];
   int n_hooked;
 };
@@ -64,13 +63,12 @@ __device__ __forceinline__ void tile_engine(TileSmem& sm, int h, int w, int32_t*
   int* par = sm.par;
   const uint32_t* be = sm.be;
   const uint32_t* bn = sm.bn;
-  int* warp_count = sm.warp_count;
   // 1. strip sweep
+  int n_pairs = 0;
   {
     const int col = warp * 32 + lane;
     const unsigned below_lanes = (1u << lane) - 1u;
     int32_t* pairs = slot + warp * PAIR_CAP;
-    int n_pairs = 0;
     int lab_below = 0;
     uint32_t upb = 0u;          // north bonds of the row below: the lanes reached from below
     for (int ly = 0; ly < h; ++ly) {
@@ -95,36 +93,28 @@ __device__ __forceinline__ void tile_engine(TileSmem& sm, int h, int w, int32_t*
       lab_below = label;
       upb = nrow;
     }
-    if (lane == 0) warp_count[warp] = n_pairs;
   }
   __syncthreads();
 
-  // 2. joins: east bonds between strips, then the listed pairs
+  // 2. joins: warp c joins the east bonds from strip c into strip c + 1 (one
+  //    row per lane), then the pairs it listed
   {
-    int total = 0;
-#pragma unroll
-    for (int k = 0; k < STRIPS; ++k) total += warp_count[k];
-    constexpr int SEAMS = TILE_H * (STRIPS - 1);
-    for (int k = threadIdx.x; k < SEAMS + total; k += LABEL_THREADS) {
-      int a, b;
-      if (k < SEAMS) {
-        const int ly = k / (STRIPS - 1), c = k - ly * (STRIPS - 1);
-        if (ly >= h) continue;
-        if (!((be[ly * STRIPS + c] >> 31) & 1u)) continue;
-        if (ly > 0) {
-          const int k0 = (ly - 1) * STRIPS + c;
-          if (((be[k0] >> 31) & 1u) && ((bn[k0] >> 31) & 1u) && (bn[k0 + 1] & 1u)) continue;   // joined below
-        }
-        a = ly * TILE_W + c * 32 + 31;
-        b = a + 1;
-      } else {
-        int j = k - SEAMS, wsel = 0;
-        while (j >= warp_count[wsel]) j -= warp_count[wsel++];
-        const int v = slot[wsel * PAIR_CAP + j];
-        a = v >> 16;
-        b = v & 0xFFFF;
+    if (warp < STRIPS - 1 && lane < h) {
+      const int ly = lane, c = warp;
+      bool join = (be[ly * STRIPS + c] >> 31) & 1u;
+      if (join && ly > 0) {
+        const int k0 = (ly - 1) * STRIPS + c;
+        if (((be[k0] >> 31) & 1u) && ((bn[k0] >> 31) & 1u) && (bn[k0 + 1] & 1u)) join = false;   // joined below
       }
-      sm_union_log(par, a, b, TILE_SITES, err, hook_log, &sm.n_hooked, TILE_SITES);
+      if (join) {
+        const int a = ly * TILE_W + c * 32 + 31;
+        sm_union_log(par, a, a + 1, TILE_SITES, err, hook_log, &sm.n_hooked, TILE_SITES);
+      }
+    }
+    const int32_t* pairs = slot + warp * PAIR_CAP;
+    for (int j = lane; j < n_pairs; j += 32) {
+      const int v = pairs[j];
+      sm_union_log(par, v >> 16, v & 0xFFFF, TILE_SITES, err, hook_log, &sm.n_hooked, TILE_SITES);
     }
   }
   __syncthreads();
