@@ -32,12 +32,12 @@ WORKLOAD = "sw_ising_q2_L%d_beta_c_hot_start_seed7"
 # DRAM traffic of k_sw_label per site from one ncu capture at L = 8192 (the
 # full-size launch is too large to capture under ncu's replay; the traffic
 # grows with the sites processed): (dram__bytes_read.sum +
-# dram__bytes_write.sum) / sites = (99.02 + 167.55) MB / 67,108,864, summary in
+# dram__bytes_write.sum) / sites = (99.46 + 167.60) MB / 67,108,864, summary in
 # profiles/k_sw_label_k_sw_flip_k_merge_L8192.md.  Valid only for the kernel
 # sources it was taken with (hash below); otherwise the line reports null.
-LABEL_TRAFFIC_BYTES_PER_SITE = 3.972
+LABEL_TRAFFIC_BYTES_PER_SITE = 3.980
 LABEL_TRAFFIC_SOURCES = ("fused_tile.cuh", "tile_engine.cuh", "k_fused.cu", "swccl_device.cuh", "swccl_shared.h")
-LABEL_TRAFFIC_SOURCE_HASH = "201b9ed1377976f5"
+LABEL_TRAFFIC_SOURCE_HASH = "f619b96790ccb9c8"
 
 
 def _label_traffic(N):
