@@ -34,21 +34,32 @@ WORKLOAD = "sw_ising_q2_L%d_beta_c_hot_start_seed7"
 # grows with the sites processed): (dram__bytes_read.sum +
 # dram__bytes_write.sum) / sites = (99.46 + 167.60) MB / 67,108,864, summary in
 # profiles/k_sw_label_k_sw_flip_k_merge_L8192.md.  Valid only for the kernel
-# sources it was taken with (hash below); otherwise the line reports null.
+# code it was taken with (label_sources_hash() below); otherwise the line
+# reports null.
 LABEL_TRAFFIC_BYTES_PER_SITE = 3.980
 LABEL_TRAFFIC_SOURCES = ("fused_tile.cuh", "tile_engine.cuh", "k_fused.cu", "swccl_device.cuh", "swccl_shared.h")
-LABEL_TRAFFIC_SOURCE_HASH = "f619b96790ccb9c8"
+LABEL_TRAFFIC_SOURCE_HASH = "7c2bb0965a540ec7"
+
+
+def label_sources_hash():
+    """Hash of the labeling kernel's sources, code only: `//` comments,
+    trailing blanks and empty lines are dropped, so that an edit of the
+    comments keeps the recorded capture valid."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in LABEL_TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_1105_5804_gb300", "csrc", f), encoding="utf-8") as fh:
+            for line in fh:
+                code = line.split("//", 1)[0].rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
+    return h.hexdigest()[:16]
 
 
 def _label_traffic(N):
     """Per-launch DRAM bytes of k_sw_label scaled from the capture, or None
-    if the kernel's sources changed since."""
-    import hashlib
-    h = hashlib.sha256()
-    for f in LABEL_TRAFFIC_SOURCES:
-        with open(os.path.join(ROOT, "paper_1105_5804_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    return LABEL_TRAFFIC_BYTES_PER_SITE * N if h.hexdigest()[:16] == LABEL_TRAFFIC_SOURCE_HASH else None
+    if the kernel's code changed since."""
+    return LABEL_TRAFFIC_BYTES_PER_SITE * N if label_sources_hash() == LABEL_TRAFFIC_SOURCE_HASH else None
 # Algorithmic HBM bytes per site of one fused sweep: k_sw_label reads the
 # int8 spins (1 B) and writes a 16-bit tile root (2 B); k_sw_flip reads the
 # root (2 B) and writes the spins (1 B).  Seam records and edge-root entries

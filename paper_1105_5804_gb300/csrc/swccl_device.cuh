@@ -189,8 +189,10 @@ __device__ __forceinline__ void g_find_multi(int* lab, int (&x)[U], const bool (
   }
 }
 
-// The two finds of a round walk in lock step, so that their loads are in
-// flight together.
+// Join the sets of a and b on the global array, as sm_union (atomicMin
+// hooking of the larger root under the smaller, a lost race retried with the
+// returned parent).  The two finds of a round walk in lock step, so that
+// their loads are in flight together.
 __device__ __forceinline__ void g_union(int* lab, int a, int b, int limit, int* err) {
   for (int rounds = 0; rounds <= limit; ++rounds) {
     int x[2] = {a, b};
