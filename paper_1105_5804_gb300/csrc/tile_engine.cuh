@@ -72,15 +72,16 @@ __device__ __forceinline__ void tile_engine(TileSmem& sm, int h, int w, int32_t*
     int lab_below = 0;
     uint32_t upb = 0u;          // north bonds of the row below: the lanes reached from below
     for (int ly = 0; ly < h; ++ly) {
-      const uint32_t east = be[ly * STRIPS + warp] & 0x7FFFFFFFu;   // runs stay inside the strip
+      // bit i of `ends`: lane i ends a run (no east bond to lane i + 1; bit 31
+      // always, runs stay inside the strip)
+      const uint32_t ends = ~be[ly * STRIPS + warp] | 0x80000000u;
       const uint32_t nrow = bn[ly * STRIPS + warp];
       const bool up_open = (upb >> lane) & 1u;   // north bond from the site below into this lane's site
-      const uint32_t breaks = ~east & below_lanes;
-      const int start = breaks ? 32 - __clz(breaks) : 0;
-      const int end = lane + __ffs(~east >> lane) - 1;
-      const uint32_t run = ((2u << end) - 1u) & ~((1u << start) - 1u);
-      const uint32_t reach = upb & run;
-      const int first = reach ? __ffs(reach) - 1 : lane;
+      const int start = 32 - __clz(ends & below_lanes);   // first lane of my run (clz(0) = 32)
+      // my run's lanes relative to start: up to the lowest set bit of tail
+      const uint32_t tail = ends >> start;
+      const uint32_t reach = (upb >> start) & (tail ^ (tail - 1u));   // its lanes reached from below
+      const int first = reach ? start + __ffs(reach) - 1 : lane;
       const int from_below = __shfl_sync(FULL, lab_below, first);
       const int label = reach ? from_below : ly * TILE_W + warp * 32 + start;
       par[ly * TILE_W + col] = label;
