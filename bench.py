@@ -32,13 +32,13 @@ WORKLOAD = "sw_ising_q2_L%d_beta_c_hot_start_seed7"
 # DRAM traffic of k_sw_label per site from one ncu capture at L = 8192 (the
 # full-size launch is too large to capture under ncu's replay; the traffic
 # grows with the sites processed): (dram__bytes_read.sum +
-# dram__bytes_write.sum) / sites = (99.46 + 167.60) MB / 67,108,864, summary in
+# dram__bytes_write.sum) / sites = (99.45 + 167.47) MB / 67,108,864, summary in
 # profiles/k_sw_label_k_sw_flip_k_merge_L8192.md.  Valid only for the kernel
 # code it was taken with (label_sources_hash() below); otherwise the line
 # reports null.
-LABEL_TRAFFIC_BYTES_PER_SITE = 3.980
+LABEL_TRAFFIC_BYTES_PER_SITE = 3.977
 LABEL_TRAFFIC_SOURCES = ("fused_tile.cuh", "tile_engine.cuh", "k_fused.cu", "swccl_device.cuh", "swccl_shared.h")
-LABEL_TRAFFIC_SOURCE_HASH = "7c2bb0965a540ec7"
+LABEL_TRAFFIC_SOURCE_HASH = "4e3a05ad73d002e9"
 
 
 def label_sources_hash():
