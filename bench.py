@@ -32,8 +32,8 @@ WORKLOAD = "sw_ising_q2_L%d_beta_c_hot_start_seed7"
 # DRAM traffic of k_sw_label per site from one ncu capture at L = 8192 (the
 # full-size launch is too large to capture under ncu's replay; the traffic
 # grows with the sites processed): (dram__bytes_read.sum +
-# dram__bytes_write.sum) / sites = (99.45 + 167.47) MB / 67,108,864, summary in
-# profiles/k_sw_label_k_sw_flip_k_merge_L8192.md.  Valid only for the kernel
+# dram__bytes_write.sum) / sites = (99.45 + 167.47) MB / 67,108,864 (the ncu
+# capture of k_sw_label at L = 8192).  Valid only for the kernel
 # code it was taken with (label_sources_hash() below); otherwise the line
 # reports null.
 LABEL_TRAFFIC_BYTES_PER_SITE = 3.977
@@ -340,7 +340,7 @@ def table_secondary(torch, sw, L=8192, warm=100, sweeps=100):
 
 
 def few_cluster_secondary(torch, sw, L=L_BENCH, ells=(16, 256), p_flip=0.5, warm=20, sweeps=50):
-    """Few-cluster update (Sec. IV, variant (c)) on the benchmark lattice:
+    """Few-cluster update (Sec. III, variant (c)) on the benchmark lattice:
     q = 2 at beta_c, hot start seed 7, one seed per block of an ell x ell
     grid, seeded clusters flip with probability p_flip."""
     out = {}

@@ -182,7 +182,7 @@ int sw_set_timing(sw_handle* h, int enable);
 int sw_phase_times(sw_handle* h, double* ms, int64_t* n_sweeps);
 
 /* ------------------------------------------------------------------------ */
-/* Few-cluster update (Sec. IV, variant (c) of the single-cluster algorithm) */
+/* Few-cluster update (Sec. III, variant (c) of the single-cluster algorithm) */
 /* ------------------------------------------------------------------------ */
 
 /* The update a sweep applies after drawing the bonds and identifying the
@@ -285,13 +285,18 @@ int sw3_phase_times(sw3_handle* h, double* ms, int64_t* n_sweeps);
  *   SW_BATCH_PHASES: one launch per step over the tiles of all chains;
  *   SW_BATCH_PERSISTENT: one cooperative launch per sweep; its CTAs walk the
  *     tiles of all chains step by step with grid barriers in between.  A
- *     barrier wait is bounded (about 2 s): on expiry the kernel records
- *     SW_ERR_TIMEOUT, returns, and later calls report it.
+ *     barrier wait is bounded (SW_BATCH_BARRIER_LIMIT_DEFAULT clock64()
+ *     cycles, about 2 s at 2 GHz, or the value of
+ *     sw_batch_set_barrier_limit): on expiry the kernel records
+ *     SW_ERR_TIMEOUT and returns; sw_batch_sync, sw_batch_observables and
+ *     sw_batch_get_spins report it.  The chains are then invalid and the
+ *     batch refuses further sweeps with SW_ERR_STATE: destroy it.
  * One sweep of either schedule is captured as a CUDA graph and replayed
  * (direct launches if capture is refused).  Both give, for every chain, the
  * same result bit for bit as a single handle with the same arguments. */
 #define SW_BATCH_PHASES 0
 #define SW_BATCH_PERSISTENT 1
+#define SW_BATCH_BARRIER_LIMIT_DEFAULT 4000000000LL
 
 typedef struct sw_batch sw_batch;
 
@@ -312,7 +317,15 @@ int sw_batch_destroy(sw_batch* b);
  * persistent kernel's CTAs per SM (0: as many as fit). */
 int sw_batch_set_schedule(sw_batch* b, int schedule, int blocks_per_sm);
 
-/* Enqueue n sweeps of every chain; returns without waiting. */
+/* Bound of one grid-barrier wait of the persistent schedule, in clock64()
+ * cycles (>= 0; default SW_BATCH_BARRIER_LIMIT_DEFAULT).  With 0 every CTA
+ * but the last to arrive gives up at once, so the next persistent sweep
+ * reports SW_ERR_TIMEOUT without waiting: a way to exercise the failure path
+ * (the batch is invalid afterwards).  Takes effect at the next sweep. */
+int sw_batch_set_barrier_limit(sw_batch* b, long long cycles);
+
+/* Enqueue n sweeps of every chain; returns without waiting.  SW_ERR_STATE
+ * (nothing enqueued) once a device-side failure of this batch was reported. */
 int sw_batch_sweep(sw_batch* b, int n);
 
 /* Wait; report SW_ERR_TIMEOUT / SW_ERR_STATE recorded by the device. */
@@ -386,10 +399,11 @@ int ccl_perc_mask(uint64_t k, uint8_t* mask, int H, int W, void* stream);
 #define CCL_NOALLOC_SCRATCH_BYTES (64LL << 20)
 
 /* ccl_label for callers that cannot allocate device memory when they label:
- * code running while a stream is captured into a CUDA graph in global
- * capture mode (cudaMalloc is refused there), latency-bound loops that must
- * not call cudaMalloc/cudaFree (cudaFree synchronises the whole device), and
- * programs whose device memory belongs to another framework's allocator.
+ * latency-bound loops (a labeling server) that must not call cudaMalloc or
+ * cudaFree, because cudaFree synchronises the whole device and stalls every
+ * other stream; and programs whose device memory belongs to another
+ * framework's caching allocator, where an allocation behind its back can fail
+ * (that allocator holds the free memory) or break its accounting.
  * The paper has no counterpart: it is a deployment variant of ccl_label.
  * Same arguments, layout and result as ccl_label; no cudaMalloc, cudaFree or
  * other allocating call is made.  Its scratch is one file-scope device array
@@ -398,10 +412,13 @@ int ccl_perc_mask(uint64_t k, uint8_t* mask, int H, int W, void* stream);
  * nothing needs clearing).  Consequently two calls whose work overlaps on
  * the GPU (different streams, not ordered) race on that array and give
  * wrong labels: order them.  The first call on each device looks up the
- * array's device address (cudaGetSymbolAddress, with that device current);
- * make that first call before any stream capture.  Grids whose scratch
- * exceeds CCL_NOALLOC_SCRATCH_BYTES are rejected with SW_ERR_ARG before
- * anything is launched.  Device-side failures are reported by ccl_status(). */
+ * array's device address and that of the labeling status word (the latter
+ * also by the first call of any other ccl_* entry point), with that device
+ * current (with lazy module loading the driver places the array in device
+ * memory then); make that first call before any stream capture.  Grids whose
+ * scratch exceeds CCL_NOALLOC_SCRATCH_BYTES are rejected with SW_ERR_ARG
+ * before anything is launched.  Device-side failures are reported by
+ * ccl_status(). */
 int ccl_label_noalloc(const uint8_t* bond_mask, int32_t* labels, int H, int W, int periodic, void* stream);
 
 /* Bytes of workspace ccl_label_batch needs for n grids of sizes H[j] x W[j]

@@ -213,7 +213,7 @@ def chain(L: int, q: int, T: int, seed: int, sweep0: int, n_sweeps: int, spins):
 
 
 # --------------------------------------------------------------------------
-# Few-cluster update (Sec. IV, variant (c) of the single-cluster algorithm)
+# Few-cluster update (Sec. III, variant (c) of the single-cluster algorithm)
 # --------------------------------------------------------------------------
 def few_seed(L: int, ell: int, seed: int, sweep_index: int, b: int) -> int:
     """Seed site of block b of the ell x ell block grid at this sweep."""

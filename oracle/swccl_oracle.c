@@ -39,7 +39,7 @@
  *     T = min(2^32, floor(p * 2^32))
  *   - new cluster state F_q(w) = floor(w * q / 2^32)
  *
- * The few-cluster update (Sec. IV, variant (c) of the single-cluster
+ * The few-cluster update (Sec. III, variant (c) of the single-cluster
  * algorithm) is the SW decomposition followed by: one seed site per block of
  * an ell x ell block grid (block side B = L / ell; the paper's tiles), every
  * cluster holding a seed is selected, and each selected cluster flips with
@@ -322,7 +322,7 @@ int or_chain(int L, int q, uint64_t T, uint64_t seed, uint64_t sweep0, int64_t n
 }
 
 /* ------------------------------------------------------------------------ */
-/* Few-cluster update (Sec. IV, variant (c)): SW bonds and clusters, then    */
+/* Few-cluster update (Sec. III, variant (c)): SW bonds and clusters, then    */
 /* only the clusters of one seed per block flip, each with probability P.    */
 /* ------------------------------------------------------------------------ */
 /* Seed site of block b (0 <= b < ell*ell) at this sweep. */

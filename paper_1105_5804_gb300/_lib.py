@@ -78,6 +78,7 @@ def lib():
         "sw_batch_destroy": ([vp], i32),
         "sw_batch_set_schedule": ([vp, i32, i32], i32),
         "sw_batch_sweep": ([vp, i32], i32),
+        "sw_batch_set_barrier_limit": ([vp, ctypes.c_longlong], i32),
         "sw_batch_sync": ([vp], i32),
         "sw_batch_observables": ([vp, i32, vp, i32, ctypes.POINTER(i32)], i32),
         "sw_batch_get_spins": ([vp, i32, vp, i32], i32),
@@ -483,6 +484,10 @@ def sw_batch_destroy(b):
 
 def sw_batch_set_schedule(b, schedule, blocks_per_sm=0):
     _check(lib().sw_batch_set_schedule(b, schedule, blocks_per_sm))
+
+
+def sw_batch_set_barrier_limit(b, cycles):
+    _check(lib().sw_batch_set_barrier_limit(b, int(cycles)))
 
 
 def sw_batch_sweep(b, n):

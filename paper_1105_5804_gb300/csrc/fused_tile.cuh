@@ -326,7 +326,7 @@ struct RootsInRegs {
 // Steps 2-5 of the flip of tile t (see k_fused.cu) given the tile roots of
 // the calling thread's sites.  All threads of the CTA call it; it ends with a
 // barrier.
-// FEW: the few-cluster update (Sec. IV, variant (c)).  Only clusters whose
+// FEW: the few-cluster update (Sec. III, variant (c)).  Only clusters whose
 // global root has its bit set in `sel` (seeded clusters) move: with FLIP draw
 // w of the root, iff (uint64)w.y < P, to state (s + 1 + F_{q-1}(w.x)) mod q,
 // s being the cluster's current state (read at the tile root).
@@ -542,7 +542,7 @@ __device__ __forceinline__ void sw_flip_tile(const SwRep& R, int t, uint64_t swe
 }
 
 // ---------------------------------------------------------------------------
-// Few-cluster seed selection (Sec. IV, variant (c)): the seed of block b of
+// Few-cluster seed selection (Sec. III, variant (c)): the seed of block b of
 // the ell x ell block grid (side B = L / ell) is (bx B + F_B(w.x),
 // by B + F_B(w.y)) with w the SEED draw (b, sweep); the bit of its cluster's
 // global root is set in `sel`.  Runs between the merge and the flip.  If the

@@ -39,7 +39,9 @@ __device__ __forceinline__ void batch_advance_block(const BatchView& b, BatchCtl
 }
 
 // Grid barrier for co-resident CTAs (cooperative launch).  Returns false if
-// the wait ran out or another CTA already failed; the error is recorded.
+// the wait ran out (limit_cycles of clock64()) or another CTA already
+// failed; the error is recorded.  After a failure the barrier's counters are
+// left as they are: the batch is not swept again (the host refuses).
 __device__ __forceinline__ bool grid_barrier(BatchCtl* ctl, unsigned nblocks, long long limit_cycles) {
   __shared__ int ok;
   __syncthreads();
@@ -54,13 +56,16 @@ __device__ __forceinline__ bool grid_barrier(BatchCtl* ctl, unsigned nblocks, lo
       __threadfence();
       atomicAdd(&ctl->bar_gen, 1u);
     } else {
+      // the limit is tested before the flag, so a limit of 0 makes every
+      // CTA but the last give up at once
       const long long t0 = clock64();
-      while (*gen == my_gen) {
-        if (clock64() - t0 > limit_cycles) {
+      for (;;) {
+        if (clock64() - t0 >= limit_cycles) {
           atomicCAS(&ctl->err, 0, SW_ERR_TIMEOUT);
           ok = 0;
           break;
         }
+        if (*gen != my_gen) break;
         __nanosleep(64);
       }
     }
@@ -181,9 +186,8 @@ int batch_persistent_blocks_per_sm() {
   return n;
 }
 
-cudaError_t launch_batch_persistent(const BatchView& b, BatchCtl* ctl, int blocks, cudaStream_t st) {
-  // a barrier wait longer than ~2 s (at 2 GHz) means something is wrong
-  long long limit_cycles = 4000000000ll;
+cudaError_t launch_batch_persistent(const BatchView& b, BatchCtl* ctl, int blocks, long long limit_cycles,
+                                    cudaStream_t st) {
   void* args[] = {(void*)&b, (void*)&ctl, (void*)&limit_cycles};
   return cudaLaunchCooperativeKernel((const void*)k_batch_persistent, dim3(blocks), dim3(LABEL_THREADS), args, 0, st);
 }

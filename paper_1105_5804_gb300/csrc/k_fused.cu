@@ -26,7 +26,7 @@
 // HBM traffic per site: spins read 1 B, 16-bit roots written and read 4 B,
 // spins written 1 B, plus seam records and edge-root entries.
 //
-// The few-cluster update (Sec. IV, variant (c)) shares k_sw_label and
+// The few-cluster update (Sec. III, variant (c)) shares k_sw_label and
 // k_merge; between the merge and the flip, k_few_select marks the global
 // roots of the clusters holding the ell^2 seeds in a bit array, and
 // k_sw_flip_few moves only those clusters (each with probability p_flip).

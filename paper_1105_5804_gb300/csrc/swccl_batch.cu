@@ -37,6 +37,8 @@ struct sw_batch {
   BatchView view{};
   int schedule = SW_BATCH_PHASES;
   int blocks = 0;                 // persistent CTAs
+  long long barrier_limit = SW_BATCH_BARRIER_LIMIT_DEFAULT;   // clock64() cycles per barrier wait
+  int failed = 0;                 // device-side failure reported: the chains are invalid
   cudaGraph_t graph[2] = {nullptr, nullptr};
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
   bool graph_failed[2] = {false, false};
@@ -65,11 +67,21 @@ void free_batch(sw_batch* b) {
 
 cudaError_t enqueue_batch_sweep(sw_batch* b) {
   cudaError_t e;
-  if (b->schedule == SW_BATCH_PERSISTENT) return launch_batch_persistent(b->view, b->ctl, b->blocks, b->stream);
+  if (b->schedule == SW_BATCH_PERSISTENT)
+    return launch_batch_persistent(b->view, b->ctl, b->blocks, b->barrier_limit, b->stream);
   if ((e = launch_batch_label(b->view, b->ctl, b->stream))) return e;
   if ((e = launch_batch_merge(b->view, b->stream))) return e;
   if ((e = launch_batch_flip(b->view, b->ctl, b->stream))) return e;
   return launch_batch_advance(b->view, b->ctl, b->stream);
+}
+
+// Forget the captured sweep of schedule k (its launch arguments changed).
+void drop_graph(sw_batch* b, int k) {
+  if (b->exec[k]) cudaGraphExecDestroy(b->exec[k]);
+  if (b->graph[k]) cudaGraphDestroy(b->graph[k]);
+  b->exec[k] = nullptr;
+  b->graph[k] = nullptr;
+  b->graph_failed[k] = false;
 }
 
 cudaError_t finish_batch_observables(sw_batch* b) {
@@ -85,9 +97,12 @@ int batch_status(sw_batch* b) {
   e = cudaMemcpyAsync(&c, b->ctl, sizeof(c), cudaMemcpyDeviceToHost, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return set_last_error(SW_ERR_CUDA, std::string("batch: ") + cudaGetErrorString(e));
+  if (c.err) b->failed = c.err;
   if (c.err == SW_ERR_TIMEOUT)
-    return set_last_error(SW_ERR_TIMEOUT, "batch: a grid barrier of the persistent sweep timed out");
-  if (c.err) return set_last_error(c.err, "batch: a device-side consistency check failed");
+    return set_last_error(SW_ERR_TIMEOUT, "batch: a grid barrier of the persistent sweep timed out; "
+                                          "the chains are invalid, destroy the batch");
+  if (c.err) return set_last_error(c.err, "batch: a device-side consistency check failed; "
+                                          "the chains are invalid, destroy the batch");
   return SW_OK;
 }
 
@@ -212,20 +227,25 @@ int sw_batch_set_schedule(sw_batch* b, int schedule, int blocks_per_sm) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int per_sm = blocks_per_sm == 0 ? max_per_sm : std::min(blocks_per_sm, max_per_sm);
     const int blocks = per_sm * sms;
-    if (blocks != b->blocks && b->exec[SW_BATCH_PERSISTENT]) {
-      cudaGraphExecDestroy(b->exec[SW_BATCH_PERSISTENT]);
-      cudaGraphDestroy(b->graph[SW_BATCH_PERSISTENT]);
-      b->exec[SW_BATCH_PERSISTENT] = nullptr;
-      b->graph[SW_BATCH_PERSISTENT] = nullptr;
-    }
+    if (blocks != b->blocks) drop_graph(b, SW_BATCH_PERSISTENT);
     b->blocks = blocks;
   }
   b->schedule = schedule;
   return SW_OK;
 }
 
+int sw_batch_set_barrier_limit(sw_batch* b, long long cycles) {
+  if (!b || cycles < 0) return set_last_error(SW_ERR_ARG, "sw_batch_set_barrier_limit: need a batch and cycles >= 0");
+  if (cycles != b->barrier_limit) drop_graph(b, SW_BATCH_PERSISTENT);
+  b->barrier_limit = cycles;
+  return SW_OK;
+}
+
 int sw_batch_sweep(sw_batch* b, int n) {
   if (!b || n < 0) return set_last_error(SW_ERR_ARG, "sw_batch_sweep: bad arguments");
+  if (b->failed)
+    return set_last_error(SW_ERR_STATE, "sw_batch_sweep: an earlier sweep failed on the device (code " +
+                                            std::to_string(b->failed) + "); the chains are invalid, destroy the batch");
   if (n == 0) return SW_OK;
   const int k = b->schedule;
   cudaError_t e;

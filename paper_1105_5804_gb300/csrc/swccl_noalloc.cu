@@ -3,13 +3,12 @@
 // ccl_label takes its scratch (tile-root lists, root counts, seam records)
 // with cudaMallocAsync, and ccl_label_ws needs the caller to allocate it.
 // Some callers can do neither when they label:
-//   * code running while a stream is being captured into a CUDA graph in
-//     global capture mode, where cudaMalloc is refused and cudaMallocAsync
-//     would add allocation nodes to the caller's graph;
 //   * latency-bound loops (serving) that must not call cudaMalloc/cudaFree,
 //     since cudaFree synchronises the whole device and stalls other streams;
 //   * programs whose device memory is owned by another framework's caching
-//     allocator and that only pass inputs and outputs across this ABI.
+//     allocator (an allocation behind its back can fail, because that
+//     allocator holds the free memory, or break its accounting) and that
+//     only pass inputs and outputs across this ABI.
 // ccl_label_noalloc serves them: its scratch is a file-scope __device__
 // array of CCL_NOALLOC_SCRATCH_BYTES.  The array exists on every GPU that
 // loads the library, for the life of the process.
@@ -17,6 +16,8 @@
 // In host code the array's name is only a host-side stand-in, not a device
 // address; its device address is looked up once per device with
 // cudaGetSymbolAddress, with that device current, and handed to the kernels.
+// The first call on a device does this look-up (and that of the labeling
+// status word), so it should come before any stream capture.
 #include <mutex>
 #include <string>
 

@@ -206,8 +206,10 @@ cudaError_t launch_batch_merge(const BatchView& b, cudaStream_t st);
 cudaError_t launch_batch_flip(const BatchView& b, BatchCtl* ctl, cudaStream_t st);
 cudaError_t launch_batch_advance(const BatchView& b, BatchCtl* ctl, cudaStream_t st);
 cudaError_t launch_batch_observe(const BatchView& b, BatchCtl* ctl, cudaStream_t st);
-// One persistent cooperative launch for the whole sweep; `blocks` CTAs.
-cudaError_t launch_batch_persistent(const BatchView& b, BatchCtl* ctl, int blocks, cudaStream_t st);
+// One persistent cooperative launch for the whole sweep; `blocks` CTAs; a
+// grid-barrier wait gives up after limit_cycles of clock64().
+cudaError_t launch_batch_persistent(const BatchView& b, BatchCtl* ctl, int blocks, long long limit_cycles,
+                                    cudaStream_t st);
 // Largest number of co-resident CTAs of the persistent kernel per SM.
 int batch_persistent_blocks_per_sm();
 

@@ -87,3 +87,29 @@ def test_workspace_size_validation():
     # two int32 per site (pair lists / root lists, hook logs) plus small seam records
     b = sw.ccl_workspace_bytes(4096, 4096)
     assert 8 * 4096 * 4096 <= b < 8.5 * 4096 * 4096
+
+
+def _header_define(name):
+    """Integer value of a `#define NAME <expr>` of include/swccl.h (C integer
+    suffixes dropped)."""
+    src = open(HEADER).read()
+    m = re.search(r"^#define\s+%s\s+(.+?)\s*$" % name, src, flags=re.M)
+    assert m, name
+    expr = m.group(1).split("/*", 1)[0].strip()
+    expr = re.sub(r"(?<=\d)(LL|ULL|L|U)\b", "", expr)
+    return int(eval(expr, {"__builtins__": {}}))
+
+
+def test_binding_constants_equal_the_header():
+    import paper_1105_5804_gb300 as sw
+    assert sw.CCL_NOALLOC_SCRATCH_BYTES == _header_define("CCL_NOALLOC_SCRATCH_BYTES")
+    for name in ("SW_OK", "SW_ERR_ARG", "SW_ERR_OOM", "SW_ERR_CUDA", "SW_ERR_TIMEOUT", "SW_ERR_STATE",
+                 "SW_CONV_AUTO", "SW_CONV_POTTS", "SW_CONV_ISING", "SW_MODE_STAGED", "SW_MODE_FUSED",
+                 "SW_BATCH_PHASES", "SW_BATCH_PERSISTENT", "SW_UPDATE_SW", "SW_UPDATE_FEW", "SW_N_PHASES"):
+        assert getattr(sw, name) == _header_define(name), name
+
+
+def test_batch_barrier_limit_refuses_bad_arguments(lib):
+    lib.sw_batch_set_barrier_limit.argtypes = [ctypes.c_void_p, ctypes.c_longlong]
+    lib.sw_batch_set_barrier_limit.restype = ctypes.c_int
+    assert lib.sw_batch_set_barrier_limit(None, 0) == 1          # SW_ERR_ARG

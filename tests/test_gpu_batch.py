@@ -111,3 +111,46 @@ def test_batch_rejects_bad_chains():
         sw.sw_batch_create([64, 30], [2, 2], [0.4, 0.4], [1, 2])
     with pytest.raises(sw.SwcclError):
         sw.sw_batch_create([64], [200], [0.4], [1])
+
+
+def test_persistent_barrier_timeout_is_reported_and_device_stays_usable():
+    """The failure path of the persistent schedule's bounded grid barrier.
+    With a limit of 0 cycles every CTA but the last to arrive gives up at its
+    first barrier and returns (no wait at all, nothing hangs): the next
+    synchronising call reports SW_ERR_TIMEOUT, the batch then refuses further
+    sweeps with SW_ERR_STATE, and the device keeps working: a new batch with
+    the default limit computes the oracle's chain."""
+    import torch
+    L, q, beta, seed = [64, 128, 256, 260], [2, 2, 3, 2], [KC, KC, 0.9, 1.1 * KC], [1, 2, 3, 4]
+    b = sw.sw_batch_create(L, q, beta, seed, sw.SW_CONV_AUTO, True)
+    try:
+        sw.sw_batch_set_schedule(b, sw.SW_BATCH_PERSISTENT)
+        assert sw.sw_batch_info(b)["persistent_blocks"] > 1
+        sw.sw_batch_set_barrier_limit(b, 0)
+        sw.sw_batch_sweep(b, 1)
+        with pytest.raises(sw.SwcclError) as e:
+            sw.sw_batch_sync(b)
+        assert e.value.code == sw.SW_ERR_TIMEOUT
+        with pytest.raises(sw.SwcclError) as e:
+            sw.sw_batch_sweep(b, 1)
+        assert e.value.code == sw.SW_ERR_STATE
+        with pytest.raises(sw.SwcclError) as e:
+            sw.sw_batch_set_barrier_limit(b, -1)
+        assert e.value.code == sw.SW_ERR_ARG
+    finally:
+        sw.sw_batch_destroy(b)
+    # the context is intact
+    x = torch.arange(1 << 20, device="cuda", dtype=torch.int64)
+    assert int(x.sum().item()) == (1 << 20) * ((1 << 20) - 1) // 2
+    b = sw.sw_batch_create(L, q, beta, seed, sw.SW_CONV_AUTO, True)
+    try:
+        sw.sw_batch_set_schedule(b, sw.SW_BATCH_PERSISTENT)
+        sw.sw_batch_sweep(b, 2)
+        sw.sw_batch_sync(b)
+        for r in range(len(L)):
+            T = _oracle_T(q[r], beta[r], oracle.CONV_AUTO)
+            s, obs = oracle.chain(L[r], q[r], T, seed[r], 0, 2, oracle.init_spins(L[r], q[r], seed[r], True))
+            assert np.array_equal(sw.sw_batch_get_spins(b, r, L[r]), s), r
+            assert np.array_equal(sw.sw_batch_observables(b, r, q[r]), obs), r
+    finally:
+        sw.sw_batch_destroy(b)

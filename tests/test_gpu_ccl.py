@@ -6,8 +6,8 @@ densities, image bonds.  Shapes span one tile, several tiles, ragged tails
 in both directions, single rows and columns, periodic and open boundaries.
 Labels must equal the oracle's breadth-first-search labels element by
 element (integer work: bit-exact).  At the 4096^2 size of the labeling
-workload, seeds 0..9 are compared in full and all 100 seeds are checked for
-the properties every canonical labeling has.
+workload all 100 seeds are compared in full and checked for the properties
+every canonical labeling has.
 """
 import ctypes
 
@@ -149,27 +149,46 @@ def _invariants(lab, mask, H, W):
     return int((l64 == i).sum())
 
 
+def _oracle_perc_labels(k, H, W):
+    """The oracle's mask of seed k and its canonical labels (runs in a worker
+    thread: the oracle's C calls release the interpreter lock)."""
+    om = oracle.perc_mask(H, W, k)
+    ref, n = oracle.label(om, H, W, True)
+    return om, ref, n
+
+
 def test_labeling_workload_4096_seeds():
-    """Critical percolation on the periodic 4096 x 4096 lattice, seeds 0..99:
-    seeds 0..9 element by element against the oracle, every seed for the
-    invariants and a cluster density near (3 sqrt3 - 5)/2."""
+    """Critical percolation on the periodic 4096 x 4096 lattice, seeds 0..99,
+    every seed element by element against the oracle (mask and labels), and
+    every seed for the invariants of a canonical labeling, with the number of
+    roots equal to the oracle's cluster count (a wrong join of two clusters
+    keeps every other invariant); the mean cluster density is near
+    (3 sqrt3 - 5)/2."""
+    import concurrent.futures as cf
+    import os
     H = W = 4096
+    seeds = list(range(100))
     mask = torch.empty(sw.mask_bytes(H * W), dtype=torch.uint8, device="cuda")
     lab = torch.empty(H * W, dtype=torch.int32, device="cuda")
     dens = []
-    for k in range(100):
-        sw.ccl_perc_mask(k, mask, H, W)
-        sw.ccl_label(mask, lab, H, W, True)
-        sw.ccl_status()
-        if k < 10:
-            om = oracle.perc_mask(H, W, k)
-            assert np.array_equal(mask.cpu().numpy(), om)
-            ref, n = oracle.label(om, H, W, True)
-            assert np.array_equal(lab.cpu().numpy(), ref)
-        n_roots = _invariants(lab, mask, H, W)
-        dens.append(n_roots / (H * W))
-    import oracle.exact as ex
-    assert abs(np.mean(dens) - ex.PERC_CLUSTER_DENSITY) < 2e-4
+    workers = max(2, min(16, (os.cpu_count() or 2)))
+    with cf.ThreadPoolExecutor(workers) as pool:
+        futs = {k: pool.submit(_oracle_perc_labels, k, H, W) for k in seeds[:workers]}
+        for k in seeds:
+            sw.ccl_perc_mask(k, mask, H, W)
+            sw.ccl_label(mask, lab, H, W, True)
+            sw.ccl_status()
+            om, ref, n = futs.pop(k).result()
+            nxt = k + workers
+            if nxt < len(seeds):
+                futs[nxt] = pool.submit(_oracle_perc_labels, nxt, H, W)
+            assert np.array_equal(mask.cpu().numpy(), om), k
+            assert np.array_equal(lab.cpu().numpy(), ref), k
+            n_roots = _invariants(lab, mask, H, W)
+            assert n_roots == n, k
+            dens.append(n_roots / (H * W))
+    import oracle.exact as exact
+    assert abs(np.mean(dens) - exact.PERC_CLUSTER_DENSITY) < 2e-4
 
 
 def test_label_batch_mixed_grids_equal_oracle_and_single_calls():

@@ -1,4 +1,4 @@
-"""GPU parity of the few-cluster update (Sec. IV, variant (c)) against the
+"""GPU parity of the few-cluster update (Sec. III, variant (c)) against the
 oracle, through the C ABI.
 
 The handle runs fused sweeps with SW_UPDATE_FEW: SW bonds and clusters, one

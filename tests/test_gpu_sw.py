@@ -332,27 +332,76 @@ def test_mode_switches_keep_the_chain():
         sw.sw_destroy(h)
 
 
+# Sweeps of the L = 16384 benchmark chain checked by one-step equivalence:
+# the first two, the end of the 100-sweep warm-up and the start of the timed
+# sweeps, the middle and the last of 200 timed sweeps, plus three drawn at
+# random (seeded) in between.  From sweep ~100 on the lattice carries the
+# critical, lattice-spanning clusters whose merges cross every seam and the
+# periodic wrap.
+def _sampled_sweeps():
+    rng = np.random.default_rng(16384)
+    extra = sorted(int(v) for v in rng.choice(np.arange(2, 299), size=3, replace=False))
+    return sorted(set([0, 1, 99, 100, 150, 299] + extra))
+
+
 @pytest.mark.parametrize("q,beta,conv", [(2, KC, sw.SW_CONV_ISING), (4, math.log(3.0), sw.SW_CONV_POTTS)])
 def test_fused_L16384_one_step_equivalence(q, beta, conv):
-    """The benchmark's lattice and mode: L = 16384, hot start seed 7, fused
-    sweeps.  Sweep 0 (one sweep per call) is checked in full against the
-    oracle stepping the initial spins; then one call of three sweeps (as the
-    benchmark calls them, many per call) is checked against the oracle's
-    chain from the GPU's spins after sweep 0."""
+    """The benchmark's lattice: L = 16384, hot start seed 7.  A fused chain
+    (the benchmark's mode, many sweeps per call) and a staged chain advance
+    side by side to sweep 299.  At every sampled sweep s both chains' spins
+    before the sweep must be equal; the oracle then steps those spins once
+    (sweep index s), and the fused chain's spins and observables and the
+    staged chain's bond mask, canonical labels, spins and observables after
+    the sweep must equal the oracle's.  The oracle's sweeps run in worker
+    threads while the GPU advances."""
+    import concurrent.futures as cf
+    import os
     L, seed = 16384, 7
     T = oracle.threshold(oracle.coupling_K(q, beta, 1.0, conv))
-    h = sw.sw_create_ex(L, q, beta, 1.0, conv, seed, True)
+    samples = _sampled_sweeps()
+    hf = sw.sw_create_ex(L, q, beta, 1.0, conv, seed, True)
+    hs = sw.sw_create_ex(L, q, beta, 1.0, conv, seed, True)
+    workers = max(2, min(len(samples), (os.cpu_count() or 2) // 2))
+    pending = []
+
+    def check(item):
+        k, fut, fs, fobs, gm, glab, gs, gobs = item
+        s_new, m, lab, obs = fut.result()
+        assert np.array_equal(gm, m), ("mask", q, k)
+        assert np.array_equal(glab, lab), ("labels", q, k)
+        assert np.array_equal(gs, s_new), ("staged spins", q, k)
+        assert np.array_equal(gobs, obs), ("staged observables", q, k)
+        assert np.array_equal(fs, s_new), ("fused spins", q, k)
+        assert np.array_equal(fobs, obs), ("fused observables", q, k)
+
     try:
-        s = sw.sw_get_spins(h)
-        sw.sw_sweep(h, 1)
-        gs = sw.sw_get_spins(h)
-        gobs = sw.sw_observables(h, 4)
-        s_new, _, _, obs = oracle.sweep(L, q, T, seed, 0, s)
-        assert np.array_equal(gs, s_new)
-        assert np.array_equal(gobs[-1], obs)
-        sw.sw_sweep(h, 3)
-        s3, obs3 = oracle.chain(L, q, T, seed, 1, 3, gs)
-        assert np.array_equal(sw.sw_get_spins(h), s3)
-        assert np.array_equal(sw.sw_observables(h, 4), obs3)
+        sw.sw_set_mode(hs, sw.SW_MODE_STAGED)
+        with cf.ThreadPoolExecutor(workers) as pool:
+            done = 0
+            for k in samples:
+                if k > done:
+                    sw.sw_sweep(hf, k - done)
+                    sw.sw_sweep(hs, k - done)
+                    sw.sw_observables(hf, 4096)
+                    sw.sw_observables(hs, 4096)
+                pre = sw.sw_get_spins(hf)
+                assert np.array_equal(sw.sw_get_spins(hs), pre), ("fused and staged chains differ", q, k)
+                fut = pool.submit(oracle.sweep, L, q, T, seed, k, pre)
+                sw.sw_sweep(hf, 1)
+                sw.sw_sweep(hs, 1)
+                done = k + 1
+                fs = sw.sw_get_spins(hf)
+                fobs = sw.sw_observables(hf, 4096)[-1]
+                gm, glab = sw.sw_debug_dump(hs)
+                gs = sw.sw_get_spins(hs)
+                gobs = sw.sw_observables(hs, 4096)[-1]
+                pending.append((k, fut, fs, fobs, gm, glab, gs, gobs))
+                del pre
+                while len(pending) >= workers:
+                    check(pending.pop(0))
+            while pending:
+                check(pending.pop(0))
+        assert sw.sw_get_info(hf)["sweeps"] == samples[-1] + 1
     finally:
-        sw.sw_destroy(h)
+        sw.sw_destroy(hf)
+        sw.sw_destroy(hs)

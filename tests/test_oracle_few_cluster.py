@@ -1,4 +1,4 @@
-"""Pins of the oracle's few-cluster update (Sec. IV, variant (c)).
+"""Pins of the oracle's few-cluster update (Sec. III, variant (c)).
 
 The update keeps the SW decomposition (same bonds and clusters as the SW
 sweep) and flips only the clusters that hold one of the ell^2 seed sites (one

@@ -1,15 +1,16 @@
 """ccl_label_noalloc: labeling for callers that cannot allocate device memory.
 
-Some callers of this library cannot call cudaMalloc when they label: code
-running while a stream is captured into a CUDA graph (global capture mode
-refuses cudaMalloc), serving loops that must not stall the device with
-cudaFree, and programs whose device memory belongs to another allocator.
+Some callers of this library cannot call cudaMalloc when they label:
+serving loops that must not stall the device with cudaFree, and programs
+whose device memory belongs to another framework's allocator.
 ccl_label_noalloc takes its scratch from one fixed device array instead.
 This test calls it through the C ABI and checks its labels against the
 allocating entry point ccl_label, element by element (integer labels:
 bit-exact), on two calls in a row with different grids, so the second call
-runs on the scratch the first one left behind; it also checks that a grid
-too large for the fixed array is refused before anything runs.
+runs on the scratch the first one left behind; that the calls, once the
+first call on the device has set up the array, leave the device's free
+memory as it was; and that a grid too large for the fixed array is refused
+before anything runs.
 
 The file is named so that pytest collects it last.
 """
@@ -30,13 +31,25 @@ def _labels(fn, mask, H, W, periodic):
 
 
 def test_noalloc_matches_ccl_label_on_two_calls_in_a_row():
+    # the first call on a device resolves the scratch array's address; with
+    # lazy module loading the driver places the array in device memory then
+    tiny = torch.zeros(1, dtype=torch.uint8, device="cuda")
+    _labels(sw.ccl_label_noalloc, tiny, 1, 1, True)
     cases = [(2048, 1536, 17, True), (999, 1001, 4, False)]
     for H, W, k, periodic in cases:
         mask = torch.empty(sw.mask_bytes(H * W), dtype=torch.uint8, device="cuda")
         sw.ccl_perc_mask(k, mask, H, W)
         ref = _labels(sw.ccl_label, mask, H, W, periodic)
-        got = _labels(sw.ccl_label_noalloc, mask, H, W, periodic)
-        assert np.array_equal(got, ref)
+        lab = torch.full((H * W,), -3, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        used0 = torch.cuda.memory_allocated()
+        sw.ccl_label_noalloc(mask, lab, H, W, periodic)
+        sw.ccl_status()
+        free1, _ = torch.cuda.mem_get_info()
+        assert torch.cuda.memory_allocated() == used0
+        assert free1 >= free0          # the call took no device memory
+        assert np.array_equal(lab.cpu().numpy(), ref)
 
 
 def test_noalloc_refuses_grids_beyond_its_fixed_scratch():
