@@ -42,18 +42,35 @@ LABEL_TRAFFIC_SOURCE_HASH = "4e3a05ad73d002e9"
 
 
 def label_sources_hash():
-    """Hash of the labeling kernel's sources, code only: `//` comments,
-    trailing blanks and empty lines are dropped, so that an edit of the
-    comments keeps the recorded capture valid."""
+    return sources_hash(LABEL_TRAFFIC_SOURCES)
+
+
+def sources_hash(files):
+    """Hash of kernel sources, code only: `//` comments, trailing blanks and
+    empty lines are dropped, so that an edit of the comments keeps a recorded
+    capture valid."""
     import hashlib
     h = hashlib.sha256()
-    for f in LABEL_TRAFFIC_SOURCES:
+    for f in files:
         with open(os.path.join(ROOT, "paper_1105_5804_gb300", "csrc", f), encoding="utf-8") as fh:
             for line in fh:
                 code = line.split("//", 1)[0].rstrip()
                 if code:
                     h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
+
+
+# DRAM traffic of the stand-alone labeling call (its three kernels) per site,
+# from an ncu capture at 4096^2, valid for the code it was taken with.
+CCL_TRAFFIC_BYTES_PER_SITE = None
+CCL_TRAFFIC_SOURCES = ("label_tile.cuh", "tile_engine.cuh", "k_label.cu", "swccl_device.cuh", "swccl_shared.h")
+CCL_TRAFFIC_SOURCE_HASH = None
+
+
+def _ccl_traffic(N):
+    if CCL_TRAFFIC_BYTES_PER_SITE is None or sources_hash(CCL_TRAFFIC_SOURCES) != CCL_TRAFFIC_SOURCE_HASH:
+        return None
+    return CCL_TRAFFIC_BYTES_PER_SITE * N
 
 
 def _label_traffic(N):
@@ -68,6 +85,8 @@ FUSED_SWEEP_BYTES_PER_SITE = 6.0
 # Philox4x32-10 calls per site made by k_sw_label: one call per pair of
 # x-adjacent sites (its four words are the pair's east and north bonds)
 LABEL_PHILOX_CALLS_PER_SITE = 0.5
+# sweeps of the separate pass that splits the sweep time by kernel
+PHASE_SWEEPS = 10
 
 
 def _peaks():
@@ -214,18 +233,22 @@ def oracle_all_cores(seconds=8.0, L=1024):
                       "%.1f s" % (cores, L, dt)}
 
 
-def oracle_ccl_sample(n_seeds=2, H=4096):
+def oracle_ccl_sample(seconds=10.0, H=4096):
     """The oracle's labeling (breadth-first search) of 4096^2 critical
-    percolation masks on one core."""
+    percolation masks (seeds 0, 1, ...) on one host core for about
+    `seconds` of labeling time (mask generation not counted)."""
     import oracle
-    masks = [oracle.perc_mask(H, H, k) for k in range(n_seeds)]
-    t0 = time.perf_counter()
-    for m in masks:
+    n, dt = 0, 0.0
+    while dt < seconds:
+        m = oracle.perc_mask(H, H, n)
+        t0 = time.perf_counter()
         oracle.label(m, H, H, True)
-    dt = time.perf_counter() - t0
-    return {"value": H * H * n_seeds / (dt * 1e9), "unit": "Gsites/s", "cores": 1,
-            "sample": "oracle labeling of %d periodic %dx%d p=1/2 masks (seeds 0..%d), %.1f s"
-                      % (n_seeds, H, H, n_seeds - 1, dt)}
+        dt += time.perf_counter() - t0
+        n += 1
+    return {"value": H * H * n / (dt * 1e9), "unit": "Gsites/s", "cores": 1, "kind": "oracle",
+            "sample": "serial oracle labeling (breadth-first search) of %d periodic %dx%d p=1/2 masks "
+                      "(seeds 0..%d) on one host core, %.1f s" % (n, H, H, n - 1, dt),
+            "cpu": _cpu_model()}
 
 
 def _cpu_model():
@@ -272,12 +295,23 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def ccl_secondary(torch, sw, n_seeds=20):
-    """Labeling workload: periodic 4096^2 critical percolation masks; each
-    label call timed alone with events, L2 flushed in between."""
-    H = W = 4096
+CCL_H = 4096
+# Algorithmic HBM bytes per site of stand-alone labeling: the packed 2-bit
+# mask read (0.25 B) and the int32 label written (4 B).
+CCL_BYTES_PER_SITE = 4.25
+
+
+def ccl_line(torch, sw, n_seeds=20, e2e_seeds=20):
+    """The labeling workload (periodic 4096^2 critical percolation masks, p =
+    1/2, seeds 0..n_seeds-1): each label call timed alone with events on the
+    launching stream, L2 flushed in between (`value`); and end to end through
+    the C ABI (`e2e`): every mask goes up from pinned host memory, is
+    labeled, and its labels come down to pinned host memory, on two copy
+    streams, double-buffered."""
+    H = W = CCL_H
     N = H * W
-    masks = torch.empty((n_seeds, sw.mask_bytes(N)), dtype=torch.uint8, device="cuda")
+    mb = sw.mask_bytes(N)
+    masks = torch.empty((n_seeds, mb), dtype=torch.uint8, device="cuda")
     for k in range(n_seeds):
         sw.ccl_perc_mask(k, masks[k], H, W)
     lab = torch.empty(N, dtype=torch.int32, device="cuda")
@@ -297,10 +331,59 @@ def ccl_secondary(torch, sw, n_seeds=20):
         times.append((a, b))
     torch.cuda.synchronize()
     sw.ccl_status()
-    ms = sum(a.elapsed_time(b) for a, b in times)
-    return {"metric": "CCL Gsites/s", "workload": "ccl_perc_p0.5_periodic_4096x4096_seeds0-%d" % (n_seeds - 1),
-            "value": N * n_seeds / (ms * 1e-3) / 1e9, "unit": "Gsites/s", "ms_per_label": ms / n_seeds,
-            "l2": "flushed (256 MiB write) between labels"}
+    ms = sum(a.elapsed_time(b) for a, b in times) / n_seeds
+    value = N / (ms * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
+    achieved = CCL_BYTES_PER_SITE * N / (ms * 1e-3) / 1e9
+
+    # end to end: pinned host masks up, labels down, overlapped on two copy streams
+    host_m = [masks[k % n_seeds].cpu().pin_memory() for k in range(2)]
+    host_l = [torch.empty(N, dtype=torch.int32).pin_memory() for _ in range(2)]
+    dev_m = [torch.empty(mb, dtype=torch.uint8, device="cuda") for _ in range(2)]
+    dev_l = [torch.empty(N, dtype=torch.int32, device="cuda") for _ in range(2)]
+    up, down = torch.cuda.Stream(), torch.cuda.Stream()
+    ev_up = [torch.cuda.Event() for _ in range(2)]
+    ev_lab = [torch.cuda.Event() for _ in range(2)]
+    ev_down = [torch.cuda.Event() for _ in range(2)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(up):
+        dev_m[0].copy_(host_m[0], non_blocking=True)
+        ev_up[0].record(up)
+    for k in range(e2e_seeds):
+        b = k % 2
+        if k + 1 < e2e_seeds:
+            with torch.cuda.stream(up):
+                dev_m[1 - b].copy_(host_m[(k + 1) % 2], non_blocking=True)
+                ev_up[1 - b].record(up)
+        st.wait_event(ev_up[b])
+        if k >= 2:
+            st.wait_event(ev_down[b])           # dev_l[b]'s previous download done
+        sw.ccl_label_ws(dev_m[b], dev_l[b], H, W, True, ws)
+        ev_lab[b].record(st)
+        with torch.cuda.stream(down):
+            down.wait_event(ev_lab[b])
+            host_l[b].copy_(dev_l[b], non_blocking=True)
+            ev_down[b].record(down)
+    torch.cuda.synchronize()
+    te = time.perf_counter() - t0
+    sw.ccl_status()
+    return {
+        "metric": "CCL Gsites/s", "value": value, "unit": "Gsites/s", "higher_is_better": True,
+        "workload": "ccl_perc_p0.5_periodic_%dx%d_seeds0-%d" % (H, W, n_seeds - 1), "ms_per_label": ms,
+        "l2": "flushed (256 MiB write) between labels",
+        "gpu_launches_per_label": 3,
+        "roofline": {"bound": "hbm", "kernel": "ccl_label (k_ccl_tile + k_merge + k_ccl_final)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": peak_kind,
+                     "work_model": "%.2f B/site algorithmic (2-bit mask read, int32 label written) x %d sites per "
+                                   "label call" % (CCL_BYTES_PER_SITE, N),
+                     "traffic": _ccl_traffic(N)},
+        "e2e": {"value": N * e2e_seeds / (te * 1e9), "unit": "Gsites/s", "labels": e2e_seeds,
+                "h2d_bytes_per_step": mb, "d2h_bytes_per_step": 4 * N,
+                "path": "per label: mask up from pinned host memory, ccl_label_ws, int32 labels down to pinned "
+                        "host memory; copies on two streams, double-buffered"},
+    }
 
 
 # The rows of the paper's benchmark table (Table I) at L = 8192: q, beta/beta_c
@@ -470,30 +553,44 @@ def batch_secondary(torch, sw, sweeps=50, single_sweeps=5):
     return res
 
 
-def serving_secondary(torch, rates=(10, 30, 100, 300, 1000, 2000), seconds=1.0, max_jobs=400):
+def serving_jobs(rate, seconds=6.0, min_jobs=200, max_jobs=2000):
+    """Jobs of one rate of the serving measurement: about `seconds` of the
+    stream, at least min_jobs and at most max_jobs."""
+    return int(min(max_jobs, max(min_jobs, rate * seconds)))
+
+
+def serving_secondary(torch, rates=(10, 30, 100, 300, 1000, 2000)):
     """The serving workload: a Poisson stream of segmentation jobs (H, W
     uniform in [256, 8192], windows of a blurred-noise 8-level image) and SW
-    jobs (L uniform in [128, 4096], 10 sweeps at the Ising beta_c), 80:20,
-    through the continuous-batching server with a 64 GiB budget and 4 slots.
-    The image pool is in pinned host memory.  Latency = completion (results
-    on the device) - arrival."""
+    jobs (L uniform in [128, 4096], 10 sweeps at the Ising beta_c), 80:20.
+    Two arms on the same job stream: the continuous-batching server (32 GiB
+    budget, 4 slots) and one job at a time through the single-job calls.
+    Latency = result in host memory (labels in pinned memory, observables
+    read) - arrival.  The image pool is in pinned host memory."""
     from paper_1105_5804_gb300 import inputs, serve
     # request payloads arrive in pinned host memory (a server's receive buffers)
     pool_pinned = torch.empty((8192, 8192), dtype=torch.uint8, pin_memory=True)
     pool = pool_pinned.numpy()
     pool[:] = inputs.blurred_noise_image(8192, 8192, seed=0)
-    out = {"workload": "serve_label_HW256-8192_sw_L128-4096_poisson", "budget_gib": 64, "slots": 4,
-           "payload": "pinned host image pool, windows uploaded by ccl_copy_pixels_2d", "rates": {}}
-    # warm-up: allocator, graphs, libraries
-    serve.run(serve.make_jobs(1000.0, 8, seed=99, image_pool=pool), serve.Server(64 << 30, slots=4))
+    budget = 32 << 30
+    out = {"workload": "serve_label_HW256-8192_sw_L128-4096_poisson", "budget_gib": budget >> 30, "slots": 4,
+           "payload": "pinned host image pool, windows uploaded by ccl_copy_pixels_2d",
+           "latency": "arrival to result in host memory (labels copied to pinned memory, observables read)",
+           "one_at_a_time": "the same stream, each job through ccl_label or sw_create_ex + sw_sweep + "
+                            "sw_observables + sw_destroy on one stream, finished before the next starts",
+           "rates": {}}
+    # warm-up: allocators (device and pinned host), libraries
+    serve.run(serve.make_jobs(2000.0, 200, seed=99, image_pool=pool), serve.Server(budget, slots=4))
+    serve.run_serial(serve.make_jobs(2000.0, 20, seed=98, image_pool=pool))
     for rate in rates:
-        n = int(min(max_jobs, max(20, rate * seconds)))
-        jobs = serve.make_jobs(float(rate), n, seed=0, image_pool=pool)
-        srv = serve.Server(64 << 30, slots=4)
-        done = serve.run(jobs, srv)
-        res = serve.summary(done)
+        n = serving_jobs(rate)
+        srv = serve.Server(budget, slots=4)
+        res = serve.summary(serve.run(serve.make_jobs(float(rate), n, seed=0, image_pool=pool), srv))
         res["max_concurrent_groups"] = srv.max_running
         res["peak_hbm_gib"] = srv.peak_in_use / 2 ** 30
+        one = serve.summary(serve.run_serial(serve.make_jobs(float(rate), n, seed=0, image_pool=pool)))
+        res["one_at_a_time"] = one
+        res["served_over_one_at_a_time_jobs_per_s"] = res["jobs_per_s"] / one["jobs_per_s"]
         out["rates"][str(rate)] = res
     return out
 
@@ -524,9 +621,8 @@ def run_ours(args):
     sw.sw_sync(h)
     sw.sw_observables(h, 4096)
 
-    # timed region: per-phase events on the handle's stream
-    sw.sw_set_timing(h, True)
-    sw.sw_phase_times(h)
+    # timed region: the sweeps as a user runs them (one captured CUDA graph per
+    # sweep, replayed), events on the handle's stream
     uuid = None
     try:
         uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
@@ -547,9 +643,16 @@ def run_ours(args):
     barrier()
     clk = clocks.stop(t0, t1)
     ms = max_over_ranks(ev0.elapsed_time(ev1))
+    obs = sw.sw_observables(h, 4096)
+    # phase split, in a separate untimed pass: the same sweeps launched
+    # eagerly with events between the kernels
+    sw.sw_set_timing(h, True)
+    sw.sw_phase_times(h)
+    sw.sw_sweep(h, PHASE_SWEEPS)
+    sw.sw_sync(h)
     phases, n_timed = sw.sw_phase_times(h)
     sw.sw_set_timing(h, False)
-    obs = sw.sw_observables(h, 4096)
+    sw.sw_observables(h, 4096)
     value = world * N * args.steps / (ms * 1e6)
 
     # end to end through the C ABI with host buffers: every step uploads its
@@ -608,8 +711,8 @@ def run_ours(args):
     e2e_value = world * N * e2e_steps / (te * 1e9) if e2e_steps else None
 
     secondary = {}
+    ccl = ccl_line(torch, sw) if rank == 0 and not args.no_ccl else None
     if rank == 0 and not args.no_secondary:
-        secondary["ccl"] = ccl_secondary(torch, sw)
         h4 = sw.sw_create_ex(L, 4, math.log(3.0), 1.0, sw.SW_CONV_POTTS, SEED_BENCH, True)
         sw.sw_sweep(h4, 10)
         s4 = torch.cuda.ExternalStream(sw.sw_stream(h4))
@@ -680,7 +783,10 @@ def run_ours(args):
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(args.cpu_seconds)
         line["cpu_baseline"]["all_cores"] = oracle_all_cores()
-        line["cpu_baseline"]["ccl"] = oracle_ccl_sample()
+    if ccl is not None:
+        if not args.no_cpu_baseline:
+            ccl["cpu_baseline"] = oracle_ccl_sample()
+        line["ccl"] = ccl
     print(json.dumps(line), flush=True)
 
 
@@ -694,6 +800,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-ccl", action="store_true")
     ap.add_argument("--L", type=int, default=L_BENCH,
                     help="lattice size (profiling of smaller cases only; the benchmark is L=16384)")
     args = ap.parse_args()

@@ -310,6 +310,26 @@ typedef struct sw_batch sw_batch;
 sw_batch* sw_batch_create(int n, const int* L, const int* q, const double* beta, const uint64_t* seed,
                           int convention, int hot_start, void* stream);
 
+/* Bytes of device memory a batch of these chains takes (what sw_batch_create
+ * allocates; the workspace size sw_batch_create_ws needs); -1 if a size is
+ * invalid.  L, q: host arrays of n entries. */
+int64_t sw_batch_device_bytes(int n, const int* L, const int* q);
+
+/* As sw_batch_create, with every device buffer of the batch carved from the
+ * caller's `workspace` (device memory, 256-byte aligned, at least
+ * sw_batch_device_bytes(n, L, q) bytes), so that creating the batch
+ * allocates no device memory: a server that keeps a pool of device memory
+ * admits jobs without cudaMalloc.  Returns without waiting: the
+ * initialisation is ordered on `stream`.  The workspace must outlive the
+ * batch; sw_batch_destroy does not free it.  NULL on failure. */
+sw_batch* sw_batch_create_ws(int n, const int* L, const int* q, const double* beta, const uint64_t* seed,
+                             int convention, int hot_start, void* workspace, int64_t ws_bytes, void* stream);
+
+/* enable = 0: sweeps are launched directly instead of from a captured CUDA
+ * graph (for a batch that runs only a few sweeps, the capture costs more
+ * than it saves); enable = 1 (default): capture one sweep, replay it. */
+int sw_batch_set_graph(sw_batch* b, int enable);
+
 /* Free the batch (waits for its stream).  NULL is accepted. */
 int sw_batch_destroy(sw_batch* b);
 
@@ -334,6 +354,15 @@ int sw_batch_sync(sw_batch* b);
 /* Observables of chain `replica` as sw_observables (own read position per
  * chain).  Synchronises. */
 int sw_batch_observables(sw_batch* b, int replica, int64_t* out, int max_sweeps, int* n_written);
+
+/* As sw_batch_observables, enqueued on the batch's stream without waiting:
+ * the rows go to `dst` (pinned host or device memory: a pageable
+ * destination makes the copy synchronous) once the work before them on the
+ * stream is done; *n_written is the number of rows that will arrive.  No
+ * device-status check: sw_batch_sync reports failures.  A server uses it to
+ * have the results in host memory when the batch's work completes, without
+ * a host wait per result. */
+int sw_batch_observables_async(sw_batch* b, int replica, int64_t* dst, int max_sweeps, int* n_written);
 
 /* Spins of chain `replica` (int8[L*L]) to host or device memory.  Synchronises. */
 int sw_batch_get_spins(sw_batch* b, int replica, int8_t* dst, int is_device);

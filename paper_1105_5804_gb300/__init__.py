@@ -18,7 +18,9 @@ from ._lib import (  # noqa: F401
     ccl_copy_pixels_2d,
     ccl_label_noalloc, CCL_NOALLOC_SCRATCH_BYTES, sw_probe_philox,
     SW_BATCH_PHASES, SW_BATCH_PERSISTENT, sw_batch_create, sw_batch_destroy, sw_batch_set_schedule,
-    sw_batch_set_barrier_limit, sw_batch_sweep, sw_batch_sync, sw_batch_info, sw_batch_observables, sw_batch_get_spins, sw_batch_stream,
+    sw_batch_set_barrier_limit, sw_batch_device_bytes, sw_batch_create_ws, sw_batch_set_graph, sw_batch_sweep,
+    sw_batch_sync, sw_batch_info, sw_batch_observables, sw_batch_observables_async, sw_batch_get_spins,
+    sw_batch_stream,
     ccl_batch_workspace_bytes, ccl_label_batch,
     SW3_N_PHASES, PHASE_NAMES3, sw3_create, sw3_create_ex, sw3_destroy, sw3_sweep, sw3_sync, sw3_get_info,
     sw3_observables, sw3_get_spins, sw3_set_spins, sw3_labels, sw3_stream, sw3_set_timing, sw3_phase_times,

@@ -76,11 +76,15 @@ def lib():
         "ccl_label_batch": ([i32, vp, vp, vp, vp, vp, vp, i64, vp], i32),
         "sw_batch_create": ([i32, vp, vp, vp, vp, i32, i32, vp], vp),
         "sw_batch_destroy": ([vp], i32),
+        "sw_batch_device_bytes": ([i32, vp, vp], i64),
+        "sw_batch_create_ws": ([i32, vp, vp, vp, vp, i32, i32, vp, i64, vp], vp),
+        "sw_batch_set_graph": ([vp, i32], i32),
         "sw_batch_set_schedule": ([vp, i32, i32], i32),
         "sw_batch_sweep": ([vp, i32], i32),
         "sw_batch_set_barrier_limit": ([vp, ctypes.c_longlong], i32),
         "sw_batch_sync": ([vp], i32),
         "sw_batch_observables": ([vp, i32, vp, i32, ctypes.POINTER(i32)], i32),
+        "sw_batch_observables_async": ([vp, i32, vp, i32, ctypes.POINTER(i32)], i32),
         "sw_batch_get_spins": ([vp, i32, vp, i32], i32),
         "sw_batch_info": ([vp, vp], i32),
         "sw_batch_stream": ([vp], vp),
@@ -478,6 +482,39 @@ def sw_batch_create(L, q, beta, seed, convention=SW_CONV_AUTO, hot_start=False, 
     return _handle(h)
 
 
+def sw_batch_device_bytes(L, q):
+    La = np.ascontiguousarray(L, dtype=np.int32)
+    qa = np.ascontiguousarray(q, dtype=np.int32)
+    if La.size != qa.size:
+        raise ValueError("L and q need one entry per chain")
+    n = int(lib().sw_batch_device_bytes(La.size, La.ctypes.data, qa.ctypes.data))
+    if n < 0:
+        raise SwcclError(SW_ERR_ARG, sw_last_error())
+    return n
+
+
+def sw_batch_create_ws(L, q, beta, seed, workspace, convention=SW_CONV_AUTO, hot_start=False, stream=0):
+    """As sw_batch_create with the batch's device memory taken from
+    `workspace` (a CUDA uint8 tensor of at least sw_batch_device_bytes(L, q)
+    bytes, 256-byte aligned), which must outlive the batch."""
+    import torch
+    n = len(L)
+    La = np.ascontiguousarray(L, dtype=np.int32)
+    qa = np.ascontiguousarray(q, dtype=np.int32)
+    ba = np.ascontiguousarray(beta, dtype=np.float64)
+    sa = np.ascontiguousarray(seed, dtype=np.uint64)
+    if not (La.size == qa.size == ba.size == sa.size == n):
+        raise ValueError("L, q, beta, seed need one entry per chain")
+    ws = _dev(workspace, torch.uint8, None, "workspace")
+    h = lib().sw_batch_create_ws(n, La.ctypes.data, qa.ctypes.data, ba.ctypes.data, sa.ctypes.data, convention,
+                                 1 if hot_start else 0, ws, workspace.numel(), _stream(stream))
+    return _handle(h)
+
+
+def sw_batch_set_graph(b, enable):
+    _check(lib().sw_batch_set_graph(b, 1 if enable else 0))
+
+
 def sw_batch_destroy(b):
     _check(lib().sw_batch_destroy(b))
 
@@ -510,6 +547,20 @@ def sw_batch_observables(b, replica, q, max_sweeps=4096):
     n = ctypes.c_int(0)
     _check(lib().sw_batch_observables(b, replica, out.ctypes.data, max_sweeps, ctypes.byref(n)))
     return out[: n.value]
+
+
+def sw_batch_observables_async(b, replica, q, out):
+    """Enqueue the unread observable rows of chain `replica` into `out` (a
+    pinned host or CUDA int64 tensor of shape (rows, 1 + q)); returns the
+    number of rows that will arrive when the batch's stream gets there."""
+    import torch
+    if not isinstance(out, torch.Tensor) or out.dtype != torch.int64 or not out.is_contiguous() or \
+            out.dim() != 2 or out.shape[1] != 1 + q or not (out.is_cuda or out.is_pinned()):
+        raise ValueError("out must be a contiguous int64 (rows, 1 + q) tensor in pinned host or device memory")
+    n = ctypes.c_int(0)
+    _check(lib().sw_batch_observables_async(b, replica, ctypes.c_void_p(out.data_ptr()), out.shape[0],
+                                            ctypes.byref(n)))
+    return n.value
 
 
 def sw_batch_get_spins(b, replica, L, out=None):

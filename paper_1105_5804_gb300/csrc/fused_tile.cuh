@@ -55,32 +55,48 @@ __device__ __forceinline__ void row_bonds(const int8_t* __restrict__ spins, int 
   const uint32_t east_byte = (uint32_t)(uint8_t)spins[row + xe];
   uint32_t eq_e = 0, eq_n = 0;
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    if (k < nw) {
-      const uint32_t next = (k + 1 < nw) ? s[k + 1] : east_byte;
-      eq_e |= eq4(s[k], (s[k] >> 8) | (next << 24)) << (4 * k);
-      eq_n |= eq4(s[k], n[k]) << (4 * k);
-    }
-  }
-  // observables of the spins read
-  const uint32_t valid = nvalid == 32 ? 0xFFFFFFFFu : ((1u << nvalid) - 1u);
-  rb.n_eq = __popc(eq_e & valid) + __popc(eq_n & valid);
-#pragma unroll
   for (int c = 0; c < QREG_MAX; ++c) rb.cnt[c] = 0;
-  if (q == 2) {
-    int ones = 0;
+  if (q == 2 && nw == 8) {
+    // Ising spins (bytes 0 or 1) packed one bit per site: the product puts
+    // byte k's bit 0 at bit 24 + k, nothing else reaches bits 24..27
+    uint32_t sb = 0u, nb = 0u;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) ones += (k < nw) ? __popc(s[k] & 0x01010101u) : 0;
-    rb.cnt[0] = nvalid - ones;
-    rb.cnt[1] = ones;
-  } else if (q <= QREG_MAX) {
+    for (int k = 0; k < 8; ++k) {
+      sb |= ((s[k] * 0x01020408u) >> 24) << (4 * k);
+      nb |= ((n[k] * 0x01020408u) >> 24) << (4 * k);
+    }
+    eq_e = ~(sb ^ ((sb >> 1) | ((east_byte & 1u) << 31)));
+    eq_n = ~(sb ^ nb);
+    rb.n_eq = __popc(eq_e) + __popc(eq_n);
+    rb.cnt[1] = __popc(sb);
+    rb.cnt[0] = 32 - rb.cnt[1];
+  } else {
 #pragma unroll
-    for (int c = 0; c < QREG_MAX; ++c) {
-      if (c >= q) break;
-      int m = 0;
+    for (int k = 0; k < 8; ++k) {
+      if (k < nw) {
+        const uint32_t next = (k + 1 < nw) ? s[k + 1] : east_byte;
+        eq_e |= eq4(s[k], (s[k] >> 8) | (next << 24)) << (4 * k);
+        eq_n |= eq4(s[k], n[k]) << (4 * k);
+      }
+    }
+    // observables of the spins read
+    const uint32_t valid = nvalid == 32 ? 0xFFFFFFFFu : ((1u << nvalid) - 1u);
+    rb.n_eq = __popc(eq_e & valid) + __popc(eq_n & valid);
+    if (q == 2) {
+      int ones = 0;
 #pragma unroll
-      for (int k = 0; k < 8; ++k) m += (k < nw) ? __popc(eq4(s[k], 0x01010101u * (uint32_t)c)) : 0;
-      rb.cnt[c] = m;
+      for (int k = 0; k < 8; ++k) ones += (k < nw) ? __popc(s[k] & 0x01010101u) : 0;
+      rb.cnt[0] = nvalid - ones;
+      rb.cnt[1] = ones;
+    } else if (q <= QREG_MAX) {
+#pragma unroll
+      for (int c = 0; c < QREG_MAX; ++c) {
+        if (c >= q) break;
+        int m = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) m += (k < nw) ? __popc(eq4(s[k], 0x01010101u * (uint32_t)c)) : 0;
+        rb.cnt[c] = m;
+      }
     }
   }
   // bonds: one Philox call per pair of sites i, i+1 (words: east i, north i,
@@ -123,6 +139,41 @@ __device__ __forceinline__ void add_observables(long long n_eq, const int* cnt, 
     if (lane == 0) red[(1 + k) * NW + warp] = c;
   }
   __syncthreads();
+  if (threadIdx.x <= qreg) {
+    unsigned long long tot = 0;
+    for (int w = 0; w < NW; ++w) tot += red[threadIdx.x * NW + w];
+    if (tot && (threadIdx.x == 0 || threadIdx.x - 1 < q)) atomicAdd(slot + threadIdx.x, tot);
+  }
+  if (qreg == 0) {
+    for (int k = threadIdx.x; k < q; k += NTHREADS)
+      if (hist[k]) atomicAdd(slot + 1 + k, (unsigned long long)hist[k]);
+  }
+}
+
+// The two halves of add_observables, for a kernel that has a __syncthreads()
+// between them anyway: every warp leaves its sums in `red` ...
+template <int NTHREADS>
+__device__ __forceinline__ void observables_warp_sums(long long n_eq, const int* cnt, int qreg,
+                                                      unsigned long long* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = NTHREADS / 32;
+  unsigned long long v = (unsigned long long)n_eq;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+  if (lane == 0) red[warp] = v;
+#pragma unroll
+  for (int k = 0; k < QREG_MAX; ++k) {
+    if (k >= qreg) break;
+    unsigned long long c = (unsigned long long)cnt[k];
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(FULL, c, o);
+    if (lane == 0) red[(1 + k) * NW + warp] = c;
+  }
+}
+
+// ... and, after a barrier, the block's totals are added to the slot.
+template <int NTHREADS>
+__device__ __forceinline__ void observables_commit(int q, int qreg, unsigned long long* slot,
+                                                   const unsigned long long* red, const int* hist) {
+  constexpr int NW = NTHREADS / 32;
   if (threadIdx.x <= qreg) {
     unsigned long long tot = 0;
     for (int w = 0; w < NW; ++w) tot += red[threadIdx.x * NW + w];
@@ -201,10 +252,10 @@ __device__ __forceinline__ void sw_label_tile(const SwRep& R, int t, uint64_t sw
   int cnt[QREG];
 #pragma unroll
   for (int k = 0; k < QREG; ++k) cnt[k] = 0;
+  uint32_t we = 0u, wn = 0u;
   {
     const int ly = lane, c = warp;
     const int nvalid = min(max(w - 32 * c, 0), 32);
-    uint32_t we = 0u, wn = 0u;
     if (ly < h && nvalid > 0) {
       const int y = y0 + ly, x = x0 + 32 * c;
       RowBonds rb;
@@ -231,10 +282,16 @@ __device__ __forceinline__ void sw_label_tile(const SwRep& R, int t, uint64_t sw
     sm.be[ly * STRIPS + c] = we;
     sm.bn[ly * STRIPS + c] = wn;
   }
+  if (do_obs) observables_warp_sums<LABEL_THREADS>(n_eq, cnt, q <= QREG ? q : 0, red);
   __syncthreads();
 
-  // 2. label the tile
-  tile_engine(sm, h, w, slot, hook_log, s.err);
+  // 2. label the tile (the engine ends with a barrier)
+  tile_engine_regs(sm, we, wn, h, slot, hook_log, s.err);
+  if (do_obs) {   // observables of the spins read (the previous sweep's result)
+    unsigned long long* oslot =
+        reinterpret_cast<unsigned long long*>(R.obs + (int64_t)((sweep - 1) % (uint64_t)obs_cap) * (q + 1));
+    observables_commit<LABEL_THREADS>(q, q <= QREG ? q : 0, oslot, red, hist);
+  }
 
   // 3. tile roots as 16-bit local indices, eight sites per thread and store
   auto entry = [&](int p) -> uint32_t { return (uint32_t)sm.par[p]; };   // p = par[site]
@@ -292,14 +349,8 @@ __device__ __forceinline__ void sw_label_tile(const SwRep& R, int t, uint64_t sw
     if (lane == 0) rec[SeamLayout::N_BITS + (k >> 5)] = (int32_t)nb;
   }
 
-  // 5. observables of the spins read (the previous sweep's result)
-  if (do_obs) {
-    unsigned long long* oslot =
-        reinterpret_cast<unsigned long long*>(R.obs + (int64_t)((sweep - 1) % (uint64_t)obs_cap) * (q + 1));
-    add_observables<LABEL_THREADS>(n_eq, cnt, q, q <= QREG ? q : 0, oslot, red, hist);
-  }
   __syncthreads();
-  // 6. edge-root bits into the (now free) pair-list slot; each thread reads
+  // 5. edge-root bits into the (now free) pair-list slot; each thread reads
   //    and next clears only its own word
   slot[threadIdx.x] = (int32_t)ls.edge_bits[threadIdx.x];
 }

@@ -80,7 +80,7 @@ __device__ __forceinline__ bool grid_barrier(BatchCtl* ctl, unsigned nblocks, lo
 
 // ---------------------------------------------------------------------------
 // Phase kernels: one CTA per global tile (merge: one thread per seam bond).
-__global__ void __launch_bounds__(LABEL_THREADS) k_batch_label(BatchView b, const BatchCtl* __restrict__ ctl) {
+__global__ void __launch_bounds__(LABEL_THREADS, 5) k_batch_label(BatchView b, const BatchCtl* __restrict__ ctl) {
   __shared__ LabelTileSmem ls;
   const uint64_t sweep = ctl->sweep;
   const bool do_obs = batch_do_obs(ctl, sweep);
@@ -122,7 +122,7 @@ union PersistentSmem {
   FlipTileSmem flip;
 };
 
-__global__ void __launch_bounds__(LABEL_THREADS) k_batch_persistent(BatchView b, BatchCtl* ctl, long long limit_cycles) {
+__global__ void __launch_bounds__(LABEL_THREADS, 4) k_batch_persistent(BatchView b, BatchCtl* ctl, long long limit_cycles) {
   __shared__ PersistentSmem u;
   const uint64_t sweep = ctl->sweep;
   const bool do_obs = batch_do_obs(ctl, sweep);

@@ -221,7 +221,7 @@ k3_local(const int8_t* __restrict__ spins, uint16_t* __restrict__ lroot, int32_t
   __syncthreads();
   // 2. the engine labels the brick's planes and joins them along z
   int32_t* slot = scratch + (int64_t)blockIdx.x * 2 * TILE_SITES;
-  tile_engine(sm, k.d, TILE_W, slot, slot + TILE_SITES, err);
+  tile_engine(sm, k.d, slot, slot + TILE_SITES, err);
   // 3. +y bonds and wraps
   for (int lz = 0; lz < k.d; ++lz) {
     const int l = (lz * B3Y + ly) * B3X + lx;

@@ -35,7 +35,7 @@
 namespace swccl {
 
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(LABEL_THREADS, 4)
+__global__ void __launch_bounds__(LABEL_THREADS, 5)
 k_sw_label(SwRep R, const SwCtl* __restrict__ ctl, int obs_cap) {
   __shared__ LabelTileSmem ls;
   const uint64_t sweep = ctl->sweep;

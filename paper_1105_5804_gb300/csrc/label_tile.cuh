@@ -67,7 +67,7 @@ __device__ __forceinline__ void ccl_label_tile(const uint8_t* __restrict__ mask,
   __syncthreads();
 
   // 2-4a. label the tile
-  tile_engine(sm, h, w, slot, hook_log, s.err);
+  tile_engine(sm, h, slot, hook_log, s.err);
 
   // 4b. every site's root; global labels; root list
   constexpr int PER_T = TILE_SITES / LABEL_THREADS;

@@ -78,23 +78,16 @@ __device__ __forceinline__ int sm_find(volatile int* par, int x, int limit, int*
   return x;
 }
 
-// sm_find of two nodes at once: the walks run in lock step, so that their
-// shared-memory loads overlap; same path halving and step limit.
+// The roots of two nodes at once: the walks run in lock step, so that their
+// shared-memory loads overlap.  No path compression: inside a tile the
+// unions keep trees shallow, and the atomics that compression needs cost
+// more than the steps they save; the hooked roots are resolved at the end.
+// Same step limit as sm_find.
 __device__ __forceinline__ void sm_find2(volatile int* par, int& a, int& b, int limit, int* err) {
   int pa = par[a], pb = par[b];
   for (int steps = 0; pa != a || pb != b; ++steps) {
-    const int ga = (pa != a) ? par[pa] : pa;
-    const int gb = (pb != b) ? par[pb] : pb;
-    if (pa != a) {
-      if (ga != pa) atomicMin((int*)&par[a], ga);
-      a = pa;
-      pa = ga;
-    }
-    if (pb != b) {
-      if (gb != pb) atomicMin((int*)&par[b], gb);
-      b = pb;
-      pb = gb;
-    }
+    if (pa != a) { a = pa; pa = par[a]; }
+    if (pb != b) { b = pb; pb = par[b]; }
     if (steps > limit) { set_error(err, SW_ERR_STATE); return; }
   }
 }
@@ -117,10 +110,12 @@ __device__ __forceinline__ void sm_union(int* par, int a, int b, int limit, int*
   set_error(err, SW_ERR_STATE);
 }
 
-// As sm_union; a root that gets hooked is appended to `hooked` (count in
-// *n_hooked, capacity `cap`), so that only hooked nodes need resolving later.
-__device__ __forceinline__ void sm_union_log(int* par, int a, int b, int limit, int* err, int* hooked,
-                                             int* n_hooked, int cap) {
+// As sm_union; a root that gets hooked is appended to a log of the hooked
+// roots (count in *n_hooked), so that only hooked nodes need resolving
+// later.  Entry k goes to hooked_fast[k] (shared memory) for k < fast_cap,
+// else to hooked[k - fast_cap] (capacity cap).
+__device__ __forceinline__ void sm_union_log(int* par, int a, int b, int limit, int* err, int* hooked_fast,
+                                             int fast_cap, int* hooked, int* n_hooked, int cap) {
   volatile int* vp = par;
   for (int rounds = 0; rounds <= limit; ++rounds) {
     sm_find2(vp, a, b, limit, err);
@@ -129,7 +124,8 @@ __device__ __forceinline__ void sm_union_log(int* par, int a, int b, int limit, 
     const int old = atomicMin(&par[b], a);
     if (old == b) {
       const int k = atomicAdd(n_hooked, 1);
-      if (k < cap) hooked[k] = b;
+      if (k < fast_cap) hooked_fast[k] = b;
+      else if (k - fast_cap < cap) hooked[k - fast_cap] = b;
       else set_error(err, SW_ERR_STATE);
       return;
     }

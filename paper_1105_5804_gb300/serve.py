@@ -20,7 +20,19 @@ All computation runs in the library's kernels; torch provides device memory
 (its caching allocator) and streams.  A label job's pixels (a window of a
 host image, rows contiguous) are uploaded by one asynchronous 2-D copy on the
 group's stream; when the host image is in pinned memory the copy is a DMA
-that overlaps the server's work.
+that overlaps the server's work.  A job is done when its result is in host
+memory: a label job's labels and an sw job's observables are copied to
+pinned host memory on the group's stream before the group's completion
+event, so the server loop never waits on a copy.  Admission allocates no device memory
+through the driver: label buffers come from torch's caching allocator and an
+sw group's chains are carved from one workspace of that allocator
+(sw_batch_create_ws), so no cudaMalloc or cudaFree stalls the device while
+other groups run.
+
+run_serial() is the one-at-a-time counterpart: the same job stream, every
+job through the plain single-job calls (ccl_label; sw_create_ex, sw_sweep,
+sw_observables, sw_destroy) on one stream, each finished before the next
+starts.
 """
 import collections
 import time
@@ -30,7 +42,6 @@ import numpy as np
 from . import _lib as sw
 
 LABEL_BYTES_PER_PX = 1 + 0.25 + 4          # pixels, packed mask, labels (+ workspace, counted exactly)
-SW_BYTES_PER_SITE = 15.8                    # handle memory of one chain
 
 
 class Job:
@@ -49,7 +60,9 @@ class Job:
         if kind == "label":
             self.bytes = int(self.H * self.W * LABEL_BYTES_PER_PX) + sw.ccl_batch_workspace_bytes([self.H], [self.W])
         else:
-            self.bytes = int(self.L * self.L * SW_BYTES_PER_SITE) + 4096 * 3 * 8
+            # what a batch of this one chain allocates (a group's batch takes the
+            # sum of its chains' shares and one set of small tables)
+            self.bytes = sw.sw_batch_device_bytes([self.L], [2])
         self.t_admit = self.t_done = None
         self.labels = self.observables = self.spins = None
 
@@ -68,6 +81,7 @@ class Server:
     def __init__(self, hbm_budget_bytes, slots=4, max_group=32, keep_results=False):
         import torch
         self.torch = torch
+        self.clock = lambda: 0.0    # time since the start of run(), set by run()
         self.budget = int(hbm_budget_bytes)
         self.in_use = 0
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
@@ -140,13 +154,26 @@ class Server:
                 sw.ccl_label_batch(masks, labels, [j.H for j in jobs], [j.W for j in jobs], [False] * len(jobs),
                                    ws, st)
                 for j, lab in zip(jobs, labels):
-                    j.labels = lab
+                    # the result goes to pinned host memory on the group's stream
+                    host = torch.empty(j.H * j.W, dtype=torch.int32, pin_memory=True)
+                    host.copy_(lab, non_blocking=True)
+                    j.labels = host
+                    g.keep.append(lab)
             else:
-                b = sw.sw_batch_create([j.L for j in jobs], [2] * len(jobs), [j.beta for j in jobs],
-                                       [j.seed for j in jobs], sw.SW_CONV_ISING, True, st)
+                Ls, qs = [j.L for j in jobs], [2] * len(jobs)
+                ws = torch.empty(sw.sw_batch_device_bytes(Ls, qs), dtype=torch.uint8, device="cuda")
+                g.keep.append(ws)
+                b = sw.sw_batch_create_ws(Ls, qs, [j.beta for j in jobs], [j.seed for j in jobs], ws,
+                                          sw.SW_CONV_ISING, True, st)
+                sw.sw_batch_set_graph(b, False)     # a few sweeps: direct launches beat a capture
                 g.batch = b
                 n = max(j.sweeps for j in jobs)
                 sw.sw_batch_sweep(b, n)
+                for r, j in enumerate(jobs):
+                    # observables to pinned host memory on the group's stream
+                    host = torch.empty((n, 3), dtype=torch.int64, pin_memory=True)
+                    sw.sw_batch_observables_async(b, r, 2, host)
+                    j.observables = host
             g.event = torch.cuda.Event()
             g.event.record(st)
         self.running.append(g)
@@ -160,10 +187,11 @@ class Server:
                 still.append(g)
                 continue
             if g.kind == "sw":
-                for r, j in enumerate(g.jobs):
-                    j.observables = sw.sw_batch_observables(g.batch, r, 2)[: j.sweeps]
-                    if self.keep_results:
+                if self.keep_results:
+                    for r, j in enumerate(g.jobs):
                         j.spins = sw.sw_batch_get_spins(g.batch, r, j.L)
+                for j in g.jobs:
+                    j.observables = j.observables.numpy()[: j.sweeps]
                 sw.sw_batch_destroy(g.batch)
             else:
                 if not self.keep_results:
@@ -210,6 +238,7 @@ def run(jobs, server, time_scale=1.0):
     step the server until all are done.  Returns the completed jobs."""
     torch = server.torch
     t0 = time.perf_counter()
+    server.clock = lambda: time.perf_counter() - t0
     pending = collections.deque(sorted(jobs, key=lambda j: j.arrival))
     while pending or not server.idle():
         now = time.perf_counter() - t0
@@ -223,6 +252,50 @@ def run(jobs, server, time_scale=1.0):
     torch.cuda.synchronize()
     sw.ccl_status()             # device-side failures of any labeling group
     return server.done
+
+
+def run_serial(jobs, stream=None, keep_results=False):
+    """The one-at-a-time arm: the same jobs in arrival order, each through the
+    single-job calls on one stream and finished (result in host memory)
+    before the next starts; a job that arrives while another runs waits.
+    Returns the jobs with t_admit / t_done set (seconds from the start)."""
+    import torch
+    st = stream or torch.cuda.Stream()
+    order = sorted(jobs, key=lambda j: j.arrival)
+    t0 = time.perf_counter()
+    for j in order:
+        wait = j.arrival - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        j.t_admit = time.perf_counter() - t0
+        with torch.cuda.stream(st):
+            if j.kind == "label":
+                src = j.pixels
+                if not (isinstance(src, np.ndarray) and src.ndim == 2 and src.strides[1] == 1):
+                    src = np.ascontiguousarray(src).reshape(j.H, j.W)
+                px = torch.empty(j.H * j.W, dtype=torch.uint8, device="cuda")
+                sw.ccl_copy_pixels_2d(src, px, st)
+                m = torch.empty(sw.mask_bytes(j.H * j.W), dtype=torch.uint8, device="cuda")
+                sw.ccl_bonds_from_pixels(px, m, j.H, j.W, False, st)
+                lab = torch.empty(j.H * j.W, dtype=torch.int32, device="cuda")
+                sw.ccl_label(m, lab, j.H, j.W, False, st)
+                host = torch.empty(j.H * j.W, dtype=torch.int32, pin_memory=True)
+                host.copy_(lab, non_blocking=True)
+                st.synchronize()
+                j.labels = host if keep_results else None
+            else:
+                h = sw.sw_create_ex(j.L, 2, j.beta, 1.0, sw.SW_CONV_ISING, j.seed, True, st)
+                try:
+                    sw.sw_sweep(h, j.sweeps)
+                    j.observables = sw.sw_observables(h, j.sweeps)
+                    if keep_results:
+                        j.spins = sw.sw_get_spins(h)
+                finally:
+                    sw.sw_destroy(h)
+        j.t_done = time.perf_counter() - t0
+        j.pixels = None
+    sw.ccl_status()
+    return order
 
 
 def summary(done, time_scale=1.0):

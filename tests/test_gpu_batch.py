@@ -154,3 +154,32 @@ def test_persistent_barrier_timeout_is_reported_and_device_stays_usable():
             assert np.array_equal(sw.sw_batch_observables(b, r, q[r]), obs), r
     finally:
         sw.sw_batch_destroy(b)
+
+
+def test_batch_in_caller_workspace_without_graph_matches_oracle():
+    """sw_batch_create_ws carves the batch from a caller's device buffer (no
+    allocation by the library) and sweeps launched without a captured graph:
+    the same chains, bit for bit, as the oracle; the size query equals what
+    the call requires."""
+    import torch
+    L, q, beta, seed = [64, 100, 256, 36], [2, 3, 2, 4], [KC, 0.8, 1.1 * KC, math.log(3.0)], [5, 6, 7, 8]
+    need = sw.sw_batch_device_bytes(L, q)
+    assert need > sum(l * l for l in L)
+    with pytest.raises(sw.SwcclError):
+        sw.sw_batch_create_ws(L, q, beta, seed, torch.empty(need - 256, dtype=torch.uint8, device="cuda"),
+                              sw.SW_CONV_AUTO, True)
+    ws = torch.full((need,), 0x5A, dtype=torch.uint8, device="cuda")
+    b = sw.sw_batch_create_ws(L, q, beta, seed, ws, sw.SW_CONV_AUTO, True)
+    try:
+        sw.sw_batch_set_graph(b, False)
+        sw.sw_batch_sweep(b, 3)
+        sw.sw_batch_sync(b)
+        assert sw.sw_batch_info(b)["graph"] == 0
+        for r in range(len(L)):
+            T = _oracle_T(q[r], beta[r], oracle.CONV_AUTO)
+            s, obs = oracle.chain(L[r], q[r], T, seed[r], 0, 3, oracle.init_spins(L[r], q[r], seed[r], True))
+            assert np.array_equal(sw.sw_batch_get_spins(b, r, L[r]), s), r
+            assert np.array_equal(sw.sw_batch_observables(b, r, q[r]), obs), r
+    finally:
+        sw.sw_batch_destroy(b)
+    assert ws.numel() == need            # the caller still owns the workspace

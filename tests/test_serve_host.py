@@ -24,6 +24,14 @@ class _Event:
         return self.done
 
 
+class _HostRows:
+    def __init__(self, n):
+        self.a = np.zeros((n, 3), dtype=np.int64)
+
+    def numpy(self):
+        return self.a
+
+
 class StubServer(serve.Server):
     """serve.Server's host state without CUDA streams; launches are recorded."""
 
@@ -40,10 +48,14 @@ class StubServer(serve.Server):
         self.peak_in_use = 0
         self.max_running = 0
         self.launched = []
+        self.clock = lambda: 0.0
 
     def _launch(self, kind, jobs):
         g = serve._Group(self.free_slots.pop(), jobs, kind)
         g.event = _Event()
+        for j in jobs:
+            if kind == "sw":      # the observables' host buffer (filled by the group's stream)
+                j.observables = _HostRows(j.sweeps)
         self.running.append(g)
         self.max_running = max(self.max_running, len(self.running))
         self.launched.append((kind, [j.id for j in jobs]))
@@ -79,8 +91,7 @@ def test_admission_is_fifo_under_the_budget():
 
 
 def test_a_group_needs_a_free_slot_and_at_most_max_group_jobs(monkeypatch):
-    # a completed sw group reads its observables and frees its batch: stubs
-    monkeypatch.setattr(serve.sw, "sw_batch_observables", lambda b, r, n: np.zeros((2, 3), dtype=np.int64))
+    # a completed sw group frees its batch: stub
     monkeypatch.setattr(serve.sw, "sw_batch_destroy", lambda b: None)
     s = StubServer(1 << 40, slots=1, max_group=2)
     for j in [_label(0), _label(1), _label(2), _sw(3)]:
