@@ -580,7 +580,7 @@ def serving_secondary(torch, rates=(10, 30, 100, 300, 1000, 2000)):
                             "sw_observables + sw_destroy on one stream, finished before the next starts",
            "rates": {}}
     # warm-up: allocators (device and pinned host), libraries
-    serve.run(serve.make_jobs(2000.0, 200, seed=99, image_pool=pool), serve.Server(budget, slots=4))
+    serve.run(serve.make_jobs(2000.0, 500, seed=99, image_pool=pool), serve.Server(budget, slots=4))
     serve.run_serial(serve.make_jobs(2000.0, 20, seed=98, image_pool=pool))
     for rate in rates:
         n = serving_jobs(rate)

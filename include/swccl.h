@@ -454,10 +454,12 @@ int ccl_label_noalloc(const uint8_t* bond_mask, int32_t* labels, int H, int W, i
  * (host arrays); -1 if a size is invalid. */
 int64_t ccl_batch_workspace_bytes(int n, const int* H, const int* W);
 
-/* Label n grids in one set of launches (one launch per step over the tiles
- * of all grids); grid j: mask masks[j] -> labels labels[j] (device
- * pointers, layouts as ccl_label), H[j] x W[j], periodic[j].  The pointer
- * and size arrays are host memory, read during the call.  `workspace` is a
+/* Label n grids with one set of launches per 32 grids (one launch per step
+ * over the tiles of those grids, which the kernels receive by value, so the
+ * call copies nothing from host memory and never waits for the stream);
+ * grid j: mask masks[j] -> labels labels[j] (device pointers, layouts as
+ * ccl_label), H[j] x W[j], periodic[j].  The pointer and size arrays are
+ * host memory, read during the call.  `workspace` is a
  * device pointer of at least ccl_batch_workspace_bytes(n, H, W) bytes,
  * 256-byte aligned; calls sharing a workspace must be ordered.  Each grid's
  * labels equal what ccl_label gives for it alone.  The paper labels one

@@ -646,39 +646,36 @@ int ccl_label_batch(int n, const uint8_t* const* masks, int32_t* const* labels, 
     if (!masks[j] || !labels[j]) return fail(SW_ERR_ARG, "ccl_label_batch: null mask or label pointer");
   int* status = ccl_status_ptr();
   if (!status) return fail(SW_ERR_CUDA, "ccl_label_batch: cannot resolve the device status word");
-  char* base = static_cast<char*>(workspace);
-  CclJob* d_jobs = reinterpret_cast<CclJob*>(base);
-  int* d_tile_job = reinterpret_cast<int*>(base + al256b((int64_t)sizeof(CclJob) * n));
-  char* p = base + al256b((int64_t)sizeof(CclJob) * n) + al256b(4 * n_tiles);
-  std::vector<CclJob> jobs(n);
-  std::vector<int> tile_job((size_t)n_tiles);
-  int t0 = 0;
-  int64_t max_sites = 0;
-  for (int j = 0; j < n; ++j) {
-    const Grid g = make_grid(H[j], W[j], periodic[j]);
-    jobs[j].mask = masks[j];
-    jobs[j].labels = labels[j];
-    jobs[j].s = carve_label_scratch(g, p, status);
-    jobs[j].g = g;
-    jobs[j].tile0 = t0;
-    jobs[j].pad = 0;
-    p += al256b(label_scratch_bytes(g));
-    for (int k = 0; k < g.n_tiles(); ++k) tile_job[t0 + k] = j;
-    t0 += g.n_tiles();
-    max_sites = std::max<int64_t>(max_sites, g.n_sites());
-  }
+  // The grids go to the kernels by value, CCL_PARAM_JOBS at a time (one set
+  // of launches each): no copy from host memory, so the call never waits
+  // for the stream.  The workspace keeps room for a device-side table too.
+  char* p = static_cast<char*>(workspace) + al256b((int64_t)sizeof(CclJob) * n) + al256b(4 * n_tiles);
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // pageable sources: the copies complete before these calls return
-  CK(cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(CclJob) * n, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(d_tile_job, tile_job.data(), sizeof(int) * n_tiles, cudaMemcpyHostToDevice, st));
-  CclBatchView v;
-  v.jobs = d_jobs;
-  v.tile_job = d_tile_job;
-  v.n_jobs = n;
-  v.n_tiles = (int)n_tiles;
-  v.limit = (int)std::min<int64_t>(max_sites + 64, (int64_t)1 << 30);
-  v.pad = 0;
-  CK(launch_ccl_batch(v, st));
+  for (int j0 = 0; j0 < n; j0 += CCL_PARAM_JOBS) {
+    CclBatchView v;
+    v.n_jobs = std::min(CCL_PARAM_JOBS, n - j0);
+    int t0 = 0;
+    int64_t max_sites = 0;
+    for (int u = 0; u < v.n_jobs; ++u) {
+      const int j = j0 + u;
+      const Grid g = make_grid(H[j], W[j], periodic[j]);
+      CclJob& J = v.jobs[u];
+      J.mask = masks[j];
+      J.labels = labels[j];
+      J.s = carve_label_scratch(g, p, status);
+      J.g = g;
+      J.tile0 = t0;
+      J.pad = 0;
+      p += al256b(label_scratch_bytes(g));
+      t0 += g.n_tiles();
+      v.tile_end[u] = t0;
+      max_sites = std::max<int64_t>(max_sites, g.n_sites());
+    }
+    v.n_tiles = t0;
+    v.limit = (int)std::min<int64_t>(max_sites + 64, (int64_t)1 << 30);
+    v.pad = 0;
+    CK(launch_ccl_batch(v, st));
+  }
   return SW_OK;
 }
 

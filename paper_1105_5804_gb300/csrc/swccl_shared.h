@@ -122,9 +122,13 @@ struct CclJob {
   int pad;
 };
 
+// Up to CCL_PARAM_JOBS grids of a batched labeling call, passed to the
+// kernels by value (no host-to-device copy, so the call never waits): the
+// tile range of grid j ends at tile_end[j].
+constexpr int CCL_PARAM_JOBS = 32;
 struct CclBatchView {
-  const CclJob* jobs;
-  const int* tile_job;
+  CclJob jobs[CCL_PARAM_JOBS];
+  int tile_end[CCL_PARAM_JOBS];
   int n_jobs;
   int n_tiles;
   int limit;          // union-find step bound: largest grid's sites + 64

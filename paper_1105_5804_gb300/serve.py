@@ -44,9 +44,57 @@ from . import _lib as sw
 LABEL_BYTES_PER_PX = 1 + 0.25 + 4          # pixels, packed mask, labels (+ workspace, counted exactly)
 
 
+class PinnedPool:
+    """Pinned host buffers for results, kept for reuse.  Pinning memory
+    (cudaHostAlloc) takes milliseconds per hundred megabytes, far longer than
+    a labeling job, so a server must not pin per request.  Buffers come in
+    power-of-two size classes; a freed buffer goes back to its class.  New
+    buffers are pinned until `cap_bytes` are held, after which acquire()
+    returns None when the class is empty (the caller waits, like for device
+    memory)."""
+
+    MIN_CLASS = 16                          # 64 KiB
+
+    def __init__(self, cap_bytes):
+        self.cap = int(cap_bytes)
+        self.held = 0
+        self.free = collections.defaultdict(list)
+
+    def _cls(self, nbytes):
+        return max(self.MIN_CLASS, (max(int(nbytes), 1) - 1).bit_length())
+
+    def acquire(self, nbytes):
+        import torch
+        k = self._cls(nbytes)
+        if self.free[k]:
+            return self.free[k].pop()
+        if self.held + (1 << k) > self.cap:
+            # give up idle buffers of other sizes; if the rest is in use, wait
+            for c, bufs in self.free.items():
+                self.held -= len(bufs) << c
+                bufs.clear()
+            if self.held + (1 << k) > self.cap:
+                return None
+        self.held += 1 << k
+        return torch.empty(1 << k, dtype=torch.uint8, pin_memory=True)
+
+    def release(self, buf):
+        self.free[self._cls(buf.numel())].append(buf)
+
+
+_POOLS = {}
+
+
+def pinned_pool(cap_bytes=8 << 30):
+    """The process's pool of pinned result buffers (one per capacity)."""
+    if cap_bytes not in _POOLS:
+        _POOLS[cap_bytes] = PinnedPool(cap_bytes)
+    return _POOLS[cap_bytes]
+
+
 class Job:
     __slots__ = ("id", "kind", "arrival", "H", "W", "pixels", "L", "beta", "sweeps", "seed", "bytes",
-                 "t_admit", "t_done", "labels", "observables", "spins")
+                 "t_admit", "t_done", "labels", "observables", "spins", "host_buf")
 
     def __init__(self, jid, kind, arrival, **kw):
         self.id, self.kind, self.arrival = jid, kind, arrival
@@ -64,7 +112,7 @@ class Job:
             # sum of its chains' shares and one set of small tables)
             self.bytes = sw.sw_batch_device_bytes([self.L], [2])
         self.t_admit = self.t_done = None
-        self.labels = self.observables = self.spins = None
+        self.labels = self.observables = self.spins = self.host_buf = None
 
 
 class _Group:
@@ -78,10 +126,11 @@ class _Group:
 
 
 class Server:
-    def __init__(self, hbm_budget_bytes, slots=4, max_group=32, keep_results=False):
+    def __init__(self, hbm_budget_bytes, slots=4, max_group=32, keep_results=False, pool=None):
         import torch
         self.torch = torch
         self.clock = lambda: 0.0    # time since the start of run(), set by run()
+        self.pool = pool or pinned_pool()
         self.budget = int(hbm_budget_bytes)
         self.in_use = 0
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
@@ -117,6 +166,10 @@ class Server:
                 break
             if len(grp) >= self.max_group or self.in_use + job.bytes > self.budget:
                 break
+            if job.kind == "label":            # its labels' pinned host buffer
+                job.host_buf = self.pool.acquire(4 * job.H * job.W)
+                if job.host_buf is None:
+                    break
             self.queue.popleft()
             self.in_use += job.bytes
             job.t_admit = now
@@ -155,7 +208,7 @@ class Server:
                                    ws, st)
                 for j, lab in zip(jobs, labels):
                     # the result goes to pinned host memory on the group's stream
-                    host = torch.empty(j.H * j.W, dtype=torch.int32, pin_memory=True)
+                    host = j.host_buf[: 4 * j.H * j.W].view(torch.int32)
                     host.copy_(lab, non_blocking=True)
                     j.labels = host
                     g.keep.append(lab)
@@ -194,9 +247,13 @@ class Server:
                     j.observables = j.observables.numpy()[: j.sweeps]
                 sw.sw_batch_destroy(g.batch)
             else:
-                if not self.keep_results:
-                    for j in g.jobs:
+                for j in g.jobs:
+                    if self.keep_results:
+                        j.labels = j.labels.clone()
+                    else:
                         j.labels = None
+                    self.pool.release(j.host_buf)
+                    j.host_buf = None
             for j in g.jobs:
                 j.t_done = now
                 j.pixels = None
@@ -254,13 +311,14 @@ def run(jobs, server, time_scale=1.0):
     return server.done
 
 
-def run_serial(jobs, stream=None, keep_results=False):
+def run_serial(jobs, stream=None, keep_results=False, pool=None):
     """The one-at-a-time arm: the same jobs in arrival order, each through the
     single-job calls on one stream and finished (result in host memory)
     before the next starts; a job that arrives while another runs waits.
     Returns the jobs with t_admit / t_done set (seconds from the start)."""
     import torch
     st = stream or torch.cuda.Stream()
+    pool = pool or pinned_pool()
     order = sorted(jobs, key=lambda j: j.arrival)
     t0 = time.perf_counter()
     for j in order:
@@ -279,10 +337,14 @@ def run_serial(jobs, stream=None, keep_results=False):
                 sw.ccl_bonds_from_pixels(px, m, j.H, j.W, False, st)
                 lab = torch.empty(j.H * j.W, dtype=torch.int32, device="cuda")
                 sw.ccl_label(m, lab, j.H, j.W, False, st)
-                host = torch.empty(j.H * j.W, dtype=torch.int32, pin_memory=True)
+                buf = pool.acquire(4 * j.H * j.W)
+                if buf is None:
+                    raise RuntimeError("the pinned pool cannot hold one job's labels")
+                host = buf[: 4 * j.H * j.W].view(torch.int32)
                 host.copy_(lab, non_blocking=True)
                 st.synchronize()
-                j.labels = host if keep_results else None
+                j.labels = host.clone() if keep_results else None
+                pool.release(buf)
             else:
                 h = sw.sw_create_ex(j.L, 2, j.beta, 1.0, sw.SW_CONV_ISING, j.seed, True, st)
                 try:

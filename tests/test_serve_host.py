@@ -24,6 +24,16 @@ class _Event:
         return self.done
 
 
+class _Pool:
+    """Pinned result buffers: always available here."""
+
+    def acquire(self, nbytes):
+        return object()
+
+    def release(self, buf):
+        pass
+
+
 class _HostRows:
     def __init__(self, n):
         self.a = np.zeros((n, 3), dtype=np.int64)
@@ -49,6 +59,7 @@ class StubServer(serve.Server):
         self.max_running = 0
         self.launched = []
         self.clock = lambda: 0.0
+        self.pool = _Pool()
 
     def _launch(self, kind, jobs):
         g = serve._Group(self.free_slots.pop(), jobs, kind)
@@ -131,3 +142,26 @@ def test_a_job_larger_than_the_whole_budget_is_refused():
     s.submit(j)
     with pytest.raises(ValueError):
         s.step(0.0)
+
+
+def test_pinned_pool_reuses_buffers_by_size_class_and_respects_its_cap(monkeypatch):
+    import torch
+    made = []
+
+    def fake_empty(n, dtype=None, pin_memory=False):
+        assert pin_memory
+        t = torch.zeros(n, dtype=dtype)
+        made.append(n)
+        return t
+    monkeypatch.setattr(torch, "empty", fake_empty)
+    pool = serve.PinnedPool(cap_bytes=3 << 20)
+    a = pool.acquire(1 << 20)                 # class 1 MiB
+    b = pool.acquire((1 << 20) + 1)           # class 2 MiB
+    assert a.numel() == 1 << 20 and b.numel() == 2 << 20 and pool.held == 3 << 20
+    assert pool.acquire(100) is None          # 64 KiB more would pass the cap; nothing idle to give up
+    pool.release(a)
+    assert pool.acquire(1000 << 10) is a      # same class: the idle buffer comes back
+    pool.release(a)
+    c = pool.acquire(64 << 10)                # another class: the idle 1 MiB buffer is given up for it
+    assert c.numel() == 64 << 10 and pool.held == (2 << 20) + (64 << 10)
+    assert made == [1 << 20, 2 << 20, 64 << 10]
