@@ -579,16 +579,21 @@ def serving_secondary(torch, rates=(10, 30, 100, 300, 1000, 2000)):
            "one_at_a_time": "the same stream, each job through ccl_label or sw_create_ex + sw_sweep + "
                             "sw_observables + sw_destroy on one stream, finished before the next starts",
            "rates": {}}
+    # the same streams for every run, as a long-running server has (torch
+    # caches freed device memory per stream)
+    slots = [torch.cuda.Stream() for _ in range(4)]
+    single = torch.cuda.Stream()
     # warm-up: allocators (device and pinned host), libraries
-    serve.run(serve.make_jobs(2000.0, 500, seed=99, image_pool=pool), serve.Server(budget, slots=4))
-    serve.run_serial(serve.make_jobs(2000.0, 20, seed=98, image_pool=pool))
+    serve.run(serve.make_jobs(2000.0, 500, seed=99, image_pool=pool), serve.Server(budget, streams=slots))
+    serve.run_serial(serve.make_jobs(2000.0, 20, seed=98, image_pool=pool), stream=single)
     for rate in rates:
         n = serving_jobs(rate)
-        srv = serve.Server(budget, slots=4)
+        srv = serve.Server(budget, streams=slots)
         res = serve.summary(serve.run(serve.make_jobs(float(rate), n, seed=0, image_pool=pool), srv))
         res["max_concurrent_groups"] = srv.max_running
         res["peak_hbm_gib"] = srv.peak_in_use / 2 ** 30
-        one = serve.summary(serve.run_serial(serve.make_jobs(float(rate), n, seed=0, image_pool=pool)))
+        one = serve.summary(serve.run_serial(serve.make_jobs(float(rate), n, seed=0, image_pool=pool),
+                                             stream=single))
         res["one_at_a_time"] = one
         res["served_over_one_at_a_time_jobs_per_s"] = res["jobs_per_s"] / one["jobs_per_s"]
         out["rates"][str(rate)] = res

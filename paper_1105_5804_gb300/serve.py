@@ -45,51 +45,69 @@ LABEL_BYTES_PER_PX = 1 + 0.25 + 4          # pixels, packed mask, labels (+ work
 
 
 class PinnedPool:
-    """Pinned host buffers for results, kept for reuse.  Pinning memory
-    (cudaHostAlloc) takes milliseconds per hundred megabytes, far longer than
-    a labeling job, so a server must not pin per request.  Buffers come in
-    power-of-two size classes; a freed buffer goes back to its class.  New
-    buffers are pinned until `cap_bytes` are held, after which acquire()
-    returns None when the class is empty (the caller waits, like for device
-    memory)."""
+    """Pinned host buffers for results, carved from one pinned arena.
+    Pinning memory (cudaHostAlloc) takes milliseconds per hundred megabytes,
+    far longer than a labeling job, so a server pins once, when the pool is
+    made, and never while it serves.  The arena is managed as a buddy system
+    of power-of-two blocks (from 64 KiB): a request takes the smallest free
+    block that holds it, splitting larger ones; a freed block merges with its
+    free buddy.  acquire() returns None when no block is free (the caller
+    waits, like for device memory)."""
 
-    MIN_CLASS = 16                          # 64 KiB
+    MIN_ORDER = 16                          # 64 KiB
 
-    def __init__(self, cap_bytes):
-        self.cap = int(cap_bytes)
-        self.held = 0
-        self.free = collections.defaultdict(list)
+    def __init__(self, arena_bytes, arena=None):
+        import torch
+        top = max(self.MIN_ORDER, int(arena_bytes).bit_length() - 1)
+        self.top = min(top, 28)                # blocks of at most 256 MiB
+        n_top = max(1, int(arena_bytes) >> self.top)
+        self.size = n_top << self.top
+        self.arena = arena if arena is not None else torch.empty(self.size, dtype=torch.uint8, pin_memory=True)
+        self.free = {k: set() for k in range(self.MIN_ORDER, self.top + 1)}
+        self.free[self.top] = set(range(0, self.size, 1 << self.top))
+        self.taken = {}                        # offset -> order
 
-    def _cls(self, nbytes):
-        return max(self.MIN_CLASS, (max(int(nbytes), 1) - 1).bit_length())
+    def _order(self, nbytes):
+        return max(self.MIN_ORDER, (max(int(nbytes), 1) - 1).bit_length())
 
     def acquire(self, nbytes):
-        import torch
-        k = self._cls(nbytes)
-        if self.free[k]:
-            return self.free[k].pop()
-        if self.held + (1 << k) > self.cap:
-            # give up idle buffers of other sizes; if the rest is in use, wait
-            for c, bufs in self.free.items():
-                self.held -= len(bufs) << c
-                bufs.clear()
-            if self.held + (1 << k) > self.cap:
-                return None
-        self.held += 1 << k
-        return torch.empty(1 << k, dtype=torch.uint8, pin_memory=True)
+        k = self._order(nbytes)
+        if k > self.top:
+            raise ValueError("a result of %d bytes is larger than the pool's largest block" % nbytes)
+        j = k
+        while j <= self.top and not self.free[j]:
+            j += 1
+        if j > self.top:
+            return None
+        off = min(self.free[j])                # lowest address first: keeps the top of the arena whole
+        self.free[j].discard(off)
+        while j > k:                           # split: keep the lower half, free the upper
+            j -= 1
+            self.free[j].add(off + (1 << j))
+        self.taken[off] = k
+        return self.arena[off: off + (1 << k)]
 
     def release(self, buf):
-        self.free[self._cls(buf.numel())].append(buf)
+        off = buf.data_ptr() - self.arena.data_ptr()
+        k = self.taken.pop(off)
+        while k < self.top:
+            buddy = off ^ (1 << k)
+            if buddy not in self.free[k]:
+                break
+            self.free[k].discard(buddy)
+            off = min(off, buddy)
+            k += 1
+        self.free[k].add(off)
 
 
 _POOLS = {}
 
 
-def pinned_pool(cap_bytes=8 << 30):
-    """The process's pool of pinned result buffers (one per capacity)."""
-    if cap_bytes not in _POOLS:
-        _POOLS[cap_bytes] = PinnedPool(cap_bytes)
-    return _POOLS[cap_bytes]
+def pinned_pool(arena_bytes=12 << 30):
+    """The process's pool of pinned result buffers (one per arena size)."""
+    if arena_bytes not in _POOLS:
+        _POOLS[arena_bytes] = PinnedPool(arena_bytes)
+    return _POOLS[arena_bytes]
 
 
 class Job:
@@ -126,14 +144,19 @@ class _Group:
 
 
 class Server:
-    def __init__(self, hbm_budget_bytes, slots=4, max_group=32, keep_results=False, pool=None):
+    def __init__(self, hbm_budget_bytes, slots=4, max_group=32, keep_results=False, pool=None, streams=None):
+        """streams: the slots' CUDA streams (default: new ones).  A process
+        that runs several servers should hand them the same streams: torch's
+        caching allocator keeps freed device memory per stream, so memory
+        cached for streams that are no longer used is not reused."""
         import torch
         self.torch = torch
         self.clock = lambda: 0.0    # time since the start of run(), set by run()
         self.pool = pool or pinned_pool()
         self.budget = int(hbm_budget_bytes)
         self.in_use = 0
-        self.streams = [torch.cuda.Stream() for _ in range(slots)]
+        self.streams = list(streams) if streams is not None else [torch.cuda.Stream() for _ in range(slots)]
+        slots = len(self.streams)
         self.free_slots = list(range(slots))
         self.max_group = max_group
         self.keep_results = keep_results

@@ -144,24 +144,22 @@ def test_a_job_larger_than_the_whole_budget_is_refused():
         s.step(0.0)
 
 
-def test_pinned_pool_reuses_buffers_by_size_class_and_respects_its_cap(monkeypatch):
+def test_pinned_pool_is_a_buddy_system_over_one_arena():
     import torch
-    made = []
-
-    def fake_empty(n, dtype=None, pin_memory=False):
-        assert pin_memory
-        t = torch.zeros(n, dtype=dtype)
-        made.append(n)
-        return t
-    monkeypatch.setattr(torch, "empty", fake_empty)
-    pool = serve.PinnedPool(cap_bytes=3 << 20)
-    a = pool.acquire(1 << 20)                 # class 1 MiB
-    b = pool.acquire((1 << 20) + 1)           # class 2 MiB
-    assert a.numel() == 1 << 20 and b.numel() == 2 << 20 and pool.held == 3 << 20
-    assert pool.acquire(100) is None          # 64 KiB more would pass the cap; nothing idle to give up
+    arena = torch.zeros(4 << 20, dtype=torch.uint8)     # stands in for the pinned arena
+    pool = serve.PinnedPool(4 << 20, arena=arena)
+    assert pool.top == 22 and pool.free[22] == {0}
+    a = pool.acquire(1 << 20)                 # 1 MiB block at the start, the rest split off
+    b = pool.acquire((1 << 20) + 1)           # needs 2 MiB: the upper half
+    c = pool.acquire(100)                     # 64 KiB from the remaining 1 MiB
+    offs = [t.data_ptr() - arena.data_ptr() for t in (a, b, c)]
+    assert offs == [0, 2 << 20, 1 << 20] and b.numel() == 2 << 20 and c.numel() == 64 << 10
+    assert pool.acquire(2 << 20) is None      # no 2 MiB block left
+    pool.release(b)
+    assert pool.acquire(2 << 20).data_ptr() - arena.data_ptr() == 2 << 20
     pool.release(a)
-    assert pool.acquire(1000 << 10) is a      # same class: the idle buffer comes back
-    pool.release(a)
-    c = pool.acquire(64 << 10)                # another class: the idle 1 MiB buffer is given up for it
-    assert c.numel() == 64 << 10 and pool.held == (2 << 20) + (64 << 10)
-    assert made == [1 << 20, 2 << 20, 64 << 10]
+    pool.release(c)
+    # a and c's blocks merged back into the lower 2 MiB
+    assert 0 in pool.free[21]
+    with pytest.raises(ValueError):
+        pool.acquire(8 << 20)
