@@ -30,8 +30,9 @@ struct RowBonds {
 
 constexpr int QREG_MAX = 8;
 
+template <class Keys>
 __device__ __forceinline__ void row_bonds(const int8_t* __restrict__ spins, int L, int y, int x, int nvalid,
-                                          uint64_t T, uint32_t klo, uint32_t khi, uint32_t sw_lo, uint32_t sw_hi,
+                                          uint64_t T, const Keys& keys, uint32_t sw_lo, uint32_t sw_hi,
                                           int q, RowBonds& rb) {
   const int yn = (y + 1 == L) ? 0 : y + 1;
   const int64_t row = (int64_t)y * L, rown = (int64_t)yn * L;
@@ -112,7 +113,7 @@ __device__ __forceinline__ void row_bonds(const int8_t* __restrict__ spins, int 
 #pragma unroll
     for (int i = 0; i < 32; i += 2) {
       if (i >= nvalid) break;
-      const uint4 r = philox(make_uint4((uint32_t)((row + x + i) >> 1), sw_lo, sw_hi, TAG_BOND), klo, khi);
+      const uint4 r = philox_draw(make_uint4((uint32_t)((row + x + i) >> 1), sw_lo, sw_hi, TAG_BOND), keys);
       e |= ((uint32_t)(r.x < thr) | ((uint32_t)(r.z < thr) << 1)) << i;
       n |= ((uint32_t)(r.y < thr) | ((uint32_t)(r.w < thr) << 1)) << i;
     }
@@ -219,8 +220,9 @@ struct FlipTileSmem {
 
 // One tile of the fused draw-and-label step (see k_fused.cu).  All threads
 // of the CTA call it; it synchronises the CTA internally and on return.
+template <class Keys>
 __device__ __forceinline__ void sw_label_tile(const SwRep& R, int t, uint64_t sweep, bool do_obs, int obs_cap,
-                                              LabelTileSmem& ls) {
+                                              LabelTileSmem& ls, const Keys& keys) {
   TileSmem& sm = ls.tile;
   uint32_t& e_last = ls.e_last;
   unsigned long long* red = ls.red;
@@ -231,7 +233,7 @@ __device__ __forceinline__ void sw_label_tile(const SwRep& R, int t, uint64_t sw
   const Grid& g = R.g;
   const LabelScratch& s = R.s;
   const int q = R.q;
-  const uint64_t T = R.T, seed = R.seed;
+  const uint64_t T = R.T;
   const int L = g.W;
   const int ty = t / g.tiles_x, tx = t - ty * g.tiles_x;
   const int y0 = ty * TILE_H, x0 = tx * TILE_W;
@@ -259,8 +261,7 @@ __device__ __forceinline__ void sw_label_tile(const SwRep& R, int t, uint64_t sw
     if (ly < h && nvalid > 0) {
       const int y = y0 + ly, x = x0 + 32 * c;
       RowBonds rb;
-      row_bonds(spins, L, y, x, nvalid, T, (uint32_t)seed, (uint32_t)(seed >> 32), (uint32_t)sweep,
-                (uint32_t)(sweep >> 32), q, rb);
+      row_bonds(spins, L, y, x, nvalid, T, keys, (uint32_t)sweep, (uint32_t)(sweep >> 32), q, rb);
       we = rb.east;
       wn = rb.north;
       if (32 * c + nvalid == w) {                 // east bond leaving the tile
@@ -381,9 +382,10 @@ struct RootsInRegs {
 // global root has its bit set in `sel` (seeded clusters) move: with FLIP draw
 // w of the root, iff (uint64)w.y < P, to state (s + 1 + F_{q-1}(w.x)) mod q,
 // s being the cluster's current state (read at the tile root).
-template <bool FEW, class Roots>
+template <bool FEW, class Roots, class Keys>
 __device__ __forceinline__ void flip_tile_core(const SwRep& R, int t, uint64_t sweep, int limit, FlipTileSmem& fs,
-                                               const Roots& roots, const uint32_t* __restrict__ sel, uint64_t P) {
+                                               const Roots& roots, const uint32_t* __restrict__ sel, uint64_t P,
+                                               const Keys& keys) {
   constexpr int PASSES = FLIP_PASSES;
   uint16_t* rlist = fs.rlist;
   uint8_t* ns = fs.ns;
@@ -392,7 +394,6 @@ __device__ __forceinline__ void flip_tile_core(const SwRep& R, int t, uint64_t s
   int32_t* __restrict__ gpar = R.gpar;
   const Grid& g = R.g;
   const int q = R.q;
-  const uint64_t seed = R.seed;
   int* err = R.s.err;
   const int L = g.W;
   const int ty = t / g.tiles_x, tx = t - ty * g.tiles_x;
@@ -450,7 +451,6 @@ __device__ __forceinline__ void flip_tile_core(const SwRep& R, int t, uint64_t s
 
   // 4. one draw per tile root, keyed by its cluster's final root; a thread
   //    takes its roots two at a time, their parent walks in lock step
-  const uint32_t klo = (uint32_t)seed, khi = (uint32_t)(seed >> 32);
   constexpr int U = 2;
   for (int k0 = threadIdx.x; k0 < n_roots; k0 += U * LABEL_THREADS) {
     int r[U], Rg[U];
@@ -473,13 +473,13 @@ __device__ __forceinline__ void flip_tile_core(const SwRep& R, int t, uint64_t s
         int v = spins[(int64_t)(y0 + (r[u] >> TILE_W_LOG2)) * L + x0 + (r[u] & (TILE_W - 1))];
         if ((__ldcg(sel + (Rg[u] >> 5)) >> (Rg[u] & 31)) & 1u) {
           const uint4 d =
-              philox(make_uint4((uint32_t)Rg[u], (uint32_t)sweep, (uint32_t)(sweep >> 32), TAG_FLIP), klo, khi);
+              philox_draw(make_uint4((uint32_t)Rg[u], (uint32_t)sweep, (uint32_t)(sweep >> 32), TAG_FLIP), keys);
           if ((uint64_t)d.y < P) v = (v + 1 + state_of(d.x, q - 1)) % q;
         }
         ns[r[u]] = (uint8_t)v;
       } else {
         const uint4 d =
-            philox(make_uint4((uint32_t)Rg[u], (uint32_t)sweep, (uint32_t)(sweep >> 32), TAG_FLIP), klo, khi);
+            philox_draw(make_uint4((uint32_t)Rg[u], (uint32_t)sweep, (uint32_t)(sweep >> 32), TAG_FLIP), keys);
         ns[r[u]] = (uint8_t)state_of(d.x, q);
       }
     }
@@ -555,9 +555,10 @@ __device__ __forceinline__ void observe_tile(const SwRep& R, int t, uint64_t don
 
 // The flip of tile t with the tile roots loaded into registers (one CTA per
 // tile; also the batch kernels).
-template <bool FEW = false>
+template <bool FEW = false, class Keys = SeedKey>
 __device__ __forceinline__ void sw_flip_tile(const SwRep& R, int t, uint64_t sweep, int limit, FlipTileSmem& fs,
-                                             const uint32_t* __restrict__ sel = nullptr, uint64_t P = 0) {
+                                             const Keys& keys, const uint32_t* __restrict__ sel = nullptr,
+                                             uint64_t P = 0) {
   const uint16_t* __restrict__ lroot = R.lroot;
   const int L = R.g.W;
   const int ty = t / R.g.tiles_x, tx = t - ty * R.g.tiles_x;
@@ -589,7 +590,7 @@ __device__ __forceinline__ void sw_flip_tile(const SwRep& R, int t, uint64_t swe
     }
     roots.r4[j] = v;
   }
-  flip_tile_core<FEW>(R, t, sweep, limit, fs, roots, sel, P);
+  flip_tile_core<FEW>(R, t, sweep, limit, fs, roots, sel, P, keys);
 }
 
 // ---------------------------------------------------------------------------

@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(LABEL_THREADS, 5) k_batch_label(BatchView b, c
   const bool do_obs = batch_do_obs(ctl, sweep);
   const int gt = blockIdx.x;
   const SwRep& R = b.reps[b.tile_rep[gt]];
-  sw_label_tile(R, gt - R.tile0, sweep, do_obs, b.obs_cap, ls);
+  sw_label_tile(R, gt - R.tile0, sweep, do_obs, b.obs_cap, ls, SeedKey{(uint32_t)R.seed, (uint32_t)(R.seed >> 32)});
 }
 
 constexpr int BATCH_MERGE_THREADS = 288;   // = MERGE_PER_TILE: one CTA per tile
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(LABEL_THREADS, 6) k_batch_flip(BatchView b, co
   __shared__ FlipTileSmem fs;
   const int gt = blockIdx.x;
   const SwRep& R = b.reps[b.tile_rep[gt]];
-  sw_flip_tile(R, gt - R.tile0, ctl->sweep, b.limit, fs);
+  sw_flip_tile(R, gt - R.tile0, ctl->sweep, b.limit, fs, SeedKey{(uint32_t)R.seed, (uint32_t)(R.seed >> 32)});
 }
 
 __global__ void k_batch_advance(BatchView b, BatchCtl* ctl) { batch_advance_block(b, ctl, ctl->sweep); }
@@ -130,7 +130,8 @@ __global__ void __launch_bounds__(LABEL_THREADS, 4) k_batch_persistent(BatchView
   // 1. draw bonds and label every tile
   for (int gt = blockIdx.x; gt < b.n_tiles; gt += nb) {
     const SwRep& R = b.reps[b.tile_rep[gt]];
-    sw_label_tile(R, gt - R.tile0, sweep, do_obs, b.obs_cap, u.label);
+    sw_label_tile(R, gt - R.tile0, sweep, do_obs, b.obs_cap, u.label,
+                  SeedKey{(uint32_t)R.seed, (uint32_t)(R.seed >> 32)});
   }
   if (!grid_barrier(ctl, nb, limit_cycles)) return;
   // 2. seam merge: warp w of the CTA takes bonds 32w..32w+31 of a tile
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(LABEL_THREADS, 4) k_batch_persistent(BatchView
   // 3. flip every tile
   for (int gt = blockIdx.x; gt < b.n_tiles; gt += nb) {
     const SwRep& R = b.reps[b.tile_rep[gt]];
-    sw_flip_tile(R, gt - R.tile0, sweep, b.limit, u.flip);
+    sw_flip_tile(R, gt - R.tile0, sweep, b.limit, u.flip, SeedKey{(uint32_t)R.seed, (uint32_t)(R.seed >> 32)});
   }
   if (!grid_barrier(ctl, nb, limit_cycles)) return;
   if (blockIdx.x == 0) batch_advance_block(b, ctl, sweep);

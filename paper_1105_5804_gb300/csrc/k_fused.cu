@@ -36,23 +36,24 @@ namespace swccl {
 
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(LABEL_THREADS, 5)
-k_sw_label(SwRep R, const SwCtl* __restrict__ ctl, int obs_cap) {
+k_sw_label(SwRep R, const SwCtl* __restrict__ ctl, int obs_cap, const __grid_constant__ PhiloxKeys keys) {
   __shared__ LabelTileSmem ls;
   const uint64_t sweep = ctl->sweep;
   const bool do_obs = sweep > 0 && ctl->obs_done != (long long)(sweep - 1);
-  sw_label_tile(R, blockIdx.x, sweep, do_obs, obs_cap, ls);
+  sw_label_tile(R, blockIdx.x, sweep, do_obs, obs_cap, ls, keys);
 }
 
 __global__ void __launch_bounds__(LABEL_THREADS, 6)
-k_sw_flip(SwRep R, const SwCtl* __restrict__ ctl, int limit) {
+k_sw_flip(SwRep R, const SwCtl* __restrict__ ctl, int limit, const __grid_constant__ PhiloxKeys keys) {
   __shared__ FlipTileSmem fs;
-  sw_flip_tile(R, blockIdx.x, ctl->sweep, limit, fs);
+  sw_flip_tile(R, blockIdx.x, ctl->sweep, limit, fs, keys);
 }
 
 __global__ void __launch_bounds__(LABEL_THREADS, 6)
-k_sw_flip_few(SwRep R, const SwCtl* __restrict__ ctl, int limit, const uint32_t* __restrict__ sel, uint64_t P) {
+k_sw_flip_few(SwRep R, const SwCtl* __restrict__ ctl, int limit, const uint32_t* __restrict__ sel, uint64_t P,
+              const __grid_constant__ PhiloxKeys keys) {
   __shared__ FlipTileSmem fs;
-  sw_flip_tile<true>(R, blockIdx.x, ctl->sweep, limit, fs, sel, P);
+  sw_flip_tile<true>(R, blockIdx.x, ctl->sweep, limit, fs, keys, sel, P);
 }
 
 constexpr int SELECT_THREADS = 256;
@@ -139,7 +140,7 @@ cudaError_t launch_sw_label(const int8_t* spins, uint16_t* lroot, int32_t* gpar,
                             const LabelScratch& s, int q, uint64_t T, uint64_t seed, const SwCtl* ctl,
                             int64_t* obs, int obs_cap, cudaStream_t st) {
   const SwRep R = make_rep(const_cast<int8_t*>(spins), lroot, gpar, obs, g, s, q, T, seed);
-  k_sw_label<<<g.n_tiles(), LABEL_THREADS, 0, st>>>(R, ctl, obs_cap);
+  k_sw_label<<<g.n_tiles(), LABEL_THREADS, 0, st>>>(R, ctl, obs_cap, philox_keys(seed));
   return cudaGetLastError();
 }
 
@@ -147,7 +148,7 @@ cudaError_t launch_sw_flip(int8_t* spins, const uint16_t* lroot, int32_t* gpar, 
                            const LabelScratch& s, int q, uint64_t seed, const SwCtl* ctl, cudaStream_t st) {
   const int limit = (int)std::min<int64_t>(g.n_sites() + 64, (int64_t)1 << 30);
   const SwRep R = make_rep(spins, const_cast<uint16_t*>(lroot), gpar, nullptr, g, s, q, 0, seed);
-  k_sw_flip<<<g.n_tiles(), LABEL_THREADS, 0, st>>>(R, ctl, limit);
+  k_sw_flip<<<g.n_tiles(), LABEL_THREADS, 0, st>>>(R, ctl, limit, philox_keys(seed));
   return cudaGetLastError();
 }
 
@@ -241,7 +242,7 @@ cudaError_t launch_sw_flip_few(int8_t* spins, const uint16_t* lroot, int32_t* gp
                                const SwCtl* ctl, cudaStream_t st) {
   const int limit = (int)std::min<int64_t>(g.n_sites() + 64, (int64_t)1 << 30);
   const SwRep R = make_rep(spins, const_cast<uint16_t*>(lroot), gpar, nullptr, g, s, q, 0, seed);
-  k_sw_flip_few<<<g.n_tiles(), LABEL_THREADS, 0, st>>>(R, ctl, limit, sel, P);
+  k_sw_flip_few<<<g.n_tiles(), LABEL_THREADS, 0, st>>>(R, ctl, limit, sel, P, philox_keys(seed));
   return cudaGetLastError();
 }
 

@@ -36,6 +36,50 @@ __device__ __forceinline__ uint4 philox(uint4 ctr, uint32_t key_lo, uint32_t key
   return ctr;
 }
 
+// The ten round keys of a seed, computed once on the host and passed to a
+// kernel by value (in constant memory, read directly by the XORs of each
+// round), so that a kernel that makes many draws with one seed does not
+// recompute the key schedule per call.
+struct PhiloxKeys {
+  uint32_t lo[10], hi[10];
+};
+
+__host__ __device__ inline PhiloxKeys philox_keys(uint64_t seed) {
+  PhiloxKeys k;
+  uint32_t lo = (uint32_t)seed, hi = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    k.lo[r] = lo;
+    k.hi[r] = hi;
+    lo += 0x9E3779B9u;
+    hi += 0xBB67AE85u;
+  }
+  return k;
+}
+
+// A seed whose key schedule is computed in every call (batches: one seed
+// per lattice, read from device memory).
+struct SeedKey {
+  uint32_t lo, hi;
+};
+
+// Philox4x32-10 with the round keys given: the same rounds as philox().
+__device__ __forceinline__ uint4 philox_draw(uint4 ctr, const PhiloxKeys& k) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    const unsigned long long pa = (unsigned long long)ctr.x * 0xD2511F53ull;
+    const unsigned long long pb = (unsigned long long)ctr.z * 0xCD9E8D57ull;
+    uint4 nxt;
+    nxt.x = (uint32_t)(pb >> 32) ^ ctr.y ^ k.lo[round];
+    nxt.y = (uint32_t)pb;
+    nxt.z = (uint32_t)(pa >> 32) ^ ctr.w ^ k.hi[round];
+    nxt.w = (uint32_t)pa;
+    ctr = nxt;
+  }
+  return ctr;
+}
+
+__device__ __forceinline__ uint4 philox_draw(uint4 ctr, const SeedKey& k) { return philox(ctr, k.lo, k.hi); }
+
 __device__ __forceinline__ uint4 draw(uint32_t c0, uint64_t sweep, uint32_t tag, uint64_t seed) {
   return philox(make_uint4(c0, (uint32_t)sweep, (uint32_t)(sweep >> 32), tag), (uint32_t)seed,
                 (uint32_t)(seed >> 32));
