@@ -516,20 +516,24 @@ def batch_secondary(torch, sw, sweeps=50, single_sweeps=5):
     q = [2] * len(L)
     total = sum(l * l for l in L)
     choice = autotune.tune(L, q, beta, sw.SW_CONV_ISING, use_cache=False)
-    b = sw.sw_batch_create(L, q, beta, seed, sw.SW_CONV_ISING, False)
     res = {"workload": "sw_batch_512_ising_L64-2048_beta0.9-1.1betac", "chains": len(L), "sites": total,
            "unit": "site-updates/ns", "sweeps": sweeps, "autotune": choice}
-    try:
-        for name, sched, bps in (("phases", sw.SW_BATCH_PHASES, 0), ("persistent", sw.SW_BATCH_PERSISTENT, 0),
-                                 ("autotuned", choice["schedule"], choice["blocks_per_sm"])):
-            sw.sw_batch_set_schedule(b, sched, bps)
-            sw.sw_batch_sweep(b, 3)
-            ms = autotune.time_batch(b, sweeps)
-            res[name] = total * sweeps / (ms * 1e6)
-        res["value"] = res["autotuned"]
-        res["graph"] = bool(sw.sw_batch_info(b)["graph"])
-    finally:
-        sw.sw_batch_destroy(b)
+    for tw in sw.TILE_WIDTHS:
+        b = sw.sw_batch_create(L, q, beta, seed, sw.SW_CONV_ISING, False, tile_w=tw)
+        try:
+            runs = [("phases", sw.SW_BATCH_PHASES, 0), ("persistent", sw.SW_BATCH_PERSISTENT, 0)]
+            if tw == choice["tile_w"]:
+                runs.append(("autotuned", choice["schedule"], choice["blocks_per_sm"]))
+            for name, sched, bps in runs:
+                sw.sw_batch_set_schedule(b, sched, bps)
+                sw.sw_batch_sweep(b, 3)
+                ms = autotune.time_batch(b, sweeps)
+                key = name if name == "autotuned" else "%s_tile%d" % (name, tw)
+                res[key] = total * sweeps / (ms * 1e6)
+            res["graph"] = bool(sw.sw_batch_info(b)["graph"])
+        finally:
+            sw.sw_batch_destroy(b)
+    res["value"] = res["autotuned"]
     # the same chains, one handle each, launched one after another on one stream
     st = torch.cuda.Stream()
     hs = [sw.sw_create_ex(L[r], 2, beta[r], 1.0, sw.SW_CONV_ISING, seed[r], False, st) for r in range(len(L))]

@@ -17,7 +17,7 @@ from ._lib import (  # noqa: F401
     ccl_label, ccl_workspace_bytes, ccl_label_ws, ccl_bonds_from_pixels, ccl_perc_mask, ccl_status,
     ccl_copy_pixels_2d,
     ccl_label_noalloc, CCL_NOALLOC_SCRATCH_BYTES, sw_probe_philox,
-    SW_BATCH_PHASES, SW_BATCH_PERSISTENT, sw_batch_create, sw_batch_destroy, sw_batch_set_schedule,
+    SW_BATCH_PHASES, SW_BATCH_PERSISTENT, TILE_WIDTHS, sw_batch_create, sw_batch_destroy, sw_batch_set_schedule,
     sw_batch_set_barrier_limit, sw_batch_device_bytes, sw_batch_create_ws, sw_batch_set_graph, sw_batch_sweep,
     sw_batch_sync, sw_batch_info, sw_batch_observables, sw_batch_observables_async, sw_batch_get_spins,
     sw_batch_stream,

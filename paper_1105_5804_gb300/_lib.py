@@ -30,18 +30,26 @@ class SwcclError(RuntimeError):
         self.code = code
 
 
-_lib = None
+_libs = {}
+TILE_WIDTHS = (256, 128, 64)
 
 
-def lib():
-    """The loaded library.  Raises if it has not been built."""
-    global _lib
-    if _lib is not None:
-        return _lib
-    if not os.path.exists(LIB_PATH):
-        raise RuntimeError("libswccl.so is not built (%s); run __graft_entry__.build() "
-                           "or python -m paper_1105_5804_gb300.build" % LIB_PATH)
-    L = ctypes.CDLL(LIB_PATH)
+def _lib_path(tile_w):
+    return LIB_PATH if tile_w == 256 else os.path.join(HERE, "_build", "libswccl_w%d.so" % tile_w)
+
+
+def lib(tile_w=256):
+    """The loaded library (the build with labeling tiles tile_w wide: 256,
+    or 128 / 64 for batches).  Raises if it has not been built."""
+    if tile_w in _libs:
+        return _libs[tile_w]
+    if tile_w not in TILE_WIDTHS:
+        raise ValueError("tile width must be one of %s" % (TILE_WIDTHS,))
+    path = _lib_path(tile_w)
+    if not os.path.exists(path):
+        raise RuntimeError("%s is not built; run __graft_entry__.build() "
+                           "or python -m paper_1105_5804_gb300.build" % path)
+    L = ctypes.CDLL(path)
     vp, i32, i64, u64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
     sig = {
         "sw_last_error": ([], ctypes.c_char_p),
@@ -103,11 +111,13 @@ def lib():
         "sw3_phase_times": ([vp, vp, ctypes.POINTER(i64)], i32),
     }
     for name, (args, res) in sig.items():
+        if tile_w != 256 and name.startswith("sw3_"):
+            continue            # the narrow-tile builds have no simple-cubic kernels
         f = getattr(L, name)
         f.argtypes = args
         f.restype = res
-    _lib = L
-    return _lib
+    _libs[tile_w] = L
+    return L
 
 
 def sw_last_error():
@@ -468,8 +478,17 @@ def ccl_status():
 # ---------------------------------------------------------------------------
 # Batches of chains
 # ---------------------------------------------------------------------------
-def sw_batch_create(L, q, beta, seed, convention=SW_CONV_AUTO, hot_start=False, stream=0):
-    """L, q, beta, seed: sequences of equal length (one entry per chain)."""
+_batch_lib = {}     # batch handle -> tile width of the library that made it
+
+
+def _blib(b):
+    return lib(_batch_lib.get(b, 256))
+
+
+def sw_batch_create(L, q, beta, seed, convention=SW_CONV_AUTO, hot_start=False, stream=0, tile_w=256):
+    """L, q, beta, seed: sequences of equal length (one entry per chain).
+    tile_w: width of the labeling tiles (256, 128 or 64; the library built
+    for it runs the batch)."""
     n = len(L)
     La = np.ascontiguousarray(L, dtype=np.int32)
     qa = np.ascontiguousarray(q, dtype=np.int32)
@@ -477,23 +496,27 @@ def sw_batch_create(L, q, beta, seed, convention=SW_CONV_AUTO, hot_start=False, 
     sa = np.ascontiguousarray(seed, dtype=np.uint64)
     if not (qa.size == ba.size == sa.size == n):
         raise ValueError("L, q, beta, seed must have equal lengths")
-    h = lib().sw_batch_create(n, La.ctypes.data, qa.ctypes.data, ba.ctypes.data, sa.ctypes.data, convention,
-                              1 if hot_start else 0, _stream(stream) if stream else None)
-    return _handle(h)
+    h = lib(tile_w).sw_batch_create(n, La.ctypes.data, qa.ctypes.data, ba.ctypes.data, sa.ctypes.data,
+                                    convention, 1 if hot_start else 0, _stream(stream) if stream else None)
+    if not h:
+        raise SwcclError(SW_ERR_ARG, lib(tile_w).sw_last_error().decode())
+    _batch_lib[h] = tile_w
+    return h
 
 
-def sw_batch_device_bytes(L, q):
+def sw_batch_device_bytes(L, q, tile_w=256):
     La = np.ascontiguousarray(L, dtype=np.int32)
     qa = np.ascontiguousarray(q, dtype=np.int32)
     if La.size != qa.size:
         raise ValueError("L and q need one entry per chain")
-    n = int(lib().sw_batch_device_bytes(La.size, La.ctypes.data, qa.ctypes.data))
+    n = int(lib(tile_w).sw_batch_device_bytes(La.size, La.ctypes.data, qa.ctypes.data))
     if n < 0:
-        raise SwcclError(SW_ERR_ARG, sw_last_error())
+        raise SwcclError(SW_ERR_ARG, lib(tile_w).sw_last_error().decode())
     return n
 
 
-def sw_batch_create_ws(L, q, beta, seed, workspace, convention=SW_CONV_AUTO, hot_start=False, stream=0):
+def sw_batch_create_ws(L, q, beta, seed, workspace, convention=SW_CONV_AUTO, hot_start=False, stream=0,
+                       tile_w=256):
     """As sw_batch_create with the batch's device memory taken from
     `workspace` (a CUDA uint8 tensor of at least sw_batch_device_bytes(L, q)
     bytes, 256-byte aligned), which must outlive the batch."""
@@ -506,46 +529,58 @@ def sw_batch_create_ws(L, q, beta, seed, workspace, convention=SW_CONV_AUTO, hot
     if not (La.size == qa.size == ba.size == sa.size == n):
         raise ValueError("L, q, beta, seed need one entry per chain")
     ws = _dev(workspace, torch.uint8, None, "workspace")
-    h = lib().sw_batch_create_ws(n, La.ctypes.data, qa.ctypes.data, ba.ctypes.data, sa.ctypes.data, convention,
-                                 1 if hot_start else 0, ws, workspace.numel(), _stream(stream))
-    return _handle(h)
+    h = lib(tile_w).sw_batch_create_ws(n, La.ctypes.data, qa.ctypes.data, ba.ctypes.data, sa.ctypes.data,
+                                       convention, 1 if hot_start else 0, ws, workspace.numel(), _stream(stream))
+    if not h:
+        raise SwcclError(SW_ERR_ARG, lib(tile_w).sw_last_error().decode())
+    _batch_lib[h] = tile_w
+    return h
 
 
 def sw_batch_set_graph(b, enable):
-    _check(lib().sw_batch_set_graph(b, 1 if enable else 0))
+    _bcheck(_blib(b), _blib(b).sw_batch_set_graph(b, 1 if enable else 0))
 
 
 def sw_batch_destroy(b):
-    _check(lib().sw_batch_destroy(b))
+    L = _blib(b)
+    _batch_lib.pop(b, None)
+    _bcheck(L, L.sw_batch_destroy(b))
+
+
+def _bcheck(L, rc):
+    if rc != SW_OK:
+        raise SwcclError(rc, L.sw_last_error().decode())
 
 
 def sw_batch_set_schedule(b, schedule, blocks_per_sm=0):
-    _check(lib().sw_batch_set_schedule(b, schedule, blocks_per_sm))
+    _bcheck(_blib(b), _blib(b).sw_batch_set_schedule(b, schedule, blocks_per_sm))
 
 
 def sw_batch_set_barrier_limit(b, cycles):
-    _check(lib().sw_batch_set_barrier_limit(b, int(cycles)))
+    _bcheck(_blib(b), _blib(b).sw_batch_set_barrier_limit(b, int(cycles)))
 
 
 def sw_batch_sweep(b, n):
-    _check(lib().sw_batch_sweep(b, n))
+    _bcheck(_blib(b), _blib(b).sw_batch_sweep(b, n))
 
 
 def sw_batch_sync(b):
-    _check(lib().sw_batch_sync(b))
+    _bcheck(_blib(b), _blib(b).sw_batch_sync(b))
 
 
 def sw_batch_info(b):
     info = np.zeros(8, dtype=np.int64)
-    _check(lib().sw_batch_info(b, info.ctypes.data))
+    _bcheck(_blib(b), _blib(b).sw_batch_info(b, info.ctypes.data))
     keys = ("chains", "sites", "tiles", "sweeps", "schedule", "persistent_blocks", "graph", "obs_capacity")
-    return {k: int(v) for k, v in zip(keys, info)}
+    out = {k: int(v) for k, v in zip(keys, info)}
+    out["tile_w"] = _batch_lib.get(b, 256)
+    return out
 
 
 def sw_batch_observables(b, replica, q, max_sweeps=4096):
     out = np.zeros((max_sweeps, 1 + q), dtype=np.int64)
     n = ctypes.c_int(0)
-    _check(lib().sw_batch_observables(b, replica, out.ctypes.data, max_sweeps, ctypes.byref(n)))
+    _bcheck(_blib(b), _blib(b).sw_batch_observables(b, replica, out.ctypes.data, max_sweeps, ctypes.byref(n)))
     return out[: n.value]
 
 
@@ -558,7 +593,7 @@ def sw_batch_observables_async(b, replica, q, out):
             out.dim() != 2 or out.shape[1] != 1 + q or not (out.is_cuda or out.is_pinned()):
         raise ValueError("out must be a contiguous int64 (rows, 1 + q) tensor in pinned host or device memory")
     n = ctypes.c_int(0)
-    _check(lib().sw_batch_observables_async(b, replica, ctypes.c_void_p(out.data_ptr()), out.shape[0],
+    _bcheck(_blib(b), _blib(b).sw_batch_observables_async(b, replica, ctypes.c_void_p(out.data_ptr()), out.shape[0],
                                             ctypes.byref(n)))
     return n.value
 
@@ -566,15 +601,15 @@ def sw_batch_observables_async(b, replica, q, out):
 def sw_batch_get_spins(b, replica, L, out=None):
     if out is None or isinstance(out, np.ndarray):
         a = np.empty(L * L, dtype=np.int8) if out is None else out
-        _check(lib().sw_batch_get_spins(b, replica, a.ctypes.data, 0))
+        _bcheck(_blib(b), _blib(b).sw_batch_get_spins(b, replica, a.ctypes.data, 0))
         return a
     import torch
-    _check(lib().sw_batch_get_spins(b, replica, _dev(out, torch.int8, L * L, "out"), 1))
+    _bcheck(_blib(b), _blib(b).sw_batch_get_spins(b, replica, _dev(out, torch.int8, L * L, "out"), 1))
     return out
 
 
 def sw_batch_stream(b):
-    return int(lib().sw_batch_stream(b) or 0)
+    return int(_blib(b).sw_batch_stream(b) or 0)
 
 
 # ---------------------------------------------------------------------------

@@ -1,12 +1,17 @@
 """Autotuner for batched Swendsen-Wang chains.
 
-Picks, for a batch of chains, how one sweep is scheduled: one launch per step
-over all tiles (SW_BATCH_PHASES), or one persistent cooperative launch per
-sweep with a chosen number of CTAs per SM (SW_BATCH_PERSISTENT).  Candidates
-are timed with CUDA events on a clone of the batch (same sizes, couplings
-and states counts, other seeds), so the chains being tuned for are not
-advanced.  Results are cached in a JSON file keyed by the GPU name and the
-batch's shape (sizes, q, number of chains).
+Picks, for a batch of chains, the labeling tile shape and how one sweep is
+scheduled.  Tile shapes: 32 rows by 256, 128 or 64 columns (the library is
+built once per width); a lattice whose side is not a multiple of the width
+leaves a ragged last tile column whose threads idle, so small and odd-sized
+chains favour narrow tiles and large ones wide tiles (fewer seams to merge).
+Schedules: one launch per step over all tiles (SW_BATCH_PHASES), or one
+persistent cooperative launch per sweep with a chosen number of CTAs per SM
+(SW_BATCH_PERSISTENT; the merge runs between grid barriers).  Every
+candidate is timed with CUDA events on a clone of the batch (same sizes,
+couplings and state counts, other seeds), so the chains being tuned for are
+not advanced.  Results are cached in a JSON file keyed by the GPU name and
+the batch's shape (sizes, q, number of chains).
 """
 import hashlib
 import json
@@ -63,37 +68,49 @@ def time_batch(b, sweeps):
 
 
 def candidates(max_blocks_per_sm=4):
+    """Schedules tried for each tile width."""
     out = [{"schedule": sw.SW_BATCH_PHASES, "blocks_per_sm": 0}]
     for k in range(1, max_blocks_per_sm + 1):
         out.append({"schedule": sw.SW_BATCH_PERSISTENT, "blocks_per_sm": k})
     return out
 
 
-def tune(L, q, beta, convention=sw.SW_CONV_AUTO, sweeps=3, use_cache=True, max_blocks_per_sm=4):
-    """Best schedule for chains (L, q, beta): a dict with schedule,
-    blocks_per_sm, ms_per_sweep and all timings."""
-    key = "%s|%s" % (_gpu_name(), _signature(L, q))
+def tune(L, q, beta, convention=sw.SW_CONV_AUTO, sweeps=3, use_cache=True, max_blocks_per_sm=4,
+         tile_widths=sw.TILE_WIDTHS):
+    """Best tile width and schedule for chains (L, q, beta): a dict with
+    tile_w, schedule, blocks_per_sm, ms_per_sweep and all timings."""
+    key = "%s|%s|%s" % (_gpu_name(), _signature(L, q), ",".join(str(w) for w in tile_widths))
     db = _load() if use_cache else {}
     if use_cache and key in db:
         return dict(db[key], cached=True)
-    clone = sw.sw_batch_create(L, q, beta, [0x5EED + r for r in range(len(L))], convention, True)
     timings = []
-    try:
-        sw.sw_batch_sweep(clone, 1)                       # warm-up and graph capture
-        for c in candidates(max_blocks_per_sm):
-            sw.sw_batch_set_schedule(clone, c["schedule"], c["blocks_per_sm"])
-            sw.sw_batch_sweep(clone, 1)
-            ms = time_batch(clone, sweeps) / sweeps
-            timings.append(dict(c, ms_per_sweep=ms))
-    finally:
-        sw.sw_batch_destroy(clone)
+    for tw in tile_widths:
+        clone = sw.sw_batch_create(L, q, beta, [0x5EED + r for r in range(len(L))], convention, True, tile_w=tw)
+        try:
+            sw.sw_batch_sweep(clone, 1)                       # warm-up and graph capture
+            for c in candidates(max_blocks_per_sm):
+                sw.sw_batch_set_schedule(clone, c["schedule"], c["blocks_per_sm"])
+                sw.sw_batch_sweep(clone, 1)
+                ms = time_batch(clone, sweeps) / sweeps
+                timings.append(dict(c, tile_w=tw, ms_per_sweep=ms))
+        finally:
+            sw.sw_batch_destroy(clone)
     best = min(timings, key=lambda t: t["ms_per_sweep"])
-    res = {"schedule": best["schedule"], "blocks_per_sm": best["blocks_per_sm"],
+    res = {"tile_w": best["tile_w"], "schedule": best["schedule"], "blocks_per_sm": best["blocks_per_sm"],
            "ms_per_sweep": best["ms_per_sweep"], "timings": timings}
     if use_cache:
         db[key] = res
         _store(db)
     return dict(res, cached=False)
+
+
+def create_tuned(L, q, beta, seed, convention=sw.SW_CONV_AUTO, hot_start=False, stream=0, **tune_kw):
+    """A batch of these chains built with the tuned tile width and schedule;
+    returns (batch, choice)."""
+    choice = tune(L, q, beta, convention, **tune_kw)
+    b = sw.sw_batch_create(L, q, beta, seed, convention, hot_start, stream, tile_w=choice["tile_w"])
+    apply(b, choice)
+    return b, choice
 
 
 def apply(b, choice):

@@ -358,11 +358,13 @@ __device__ __forceinline__ void sw_label_tile(const SwRep& R, int t, uint64_t sw
 
 // One tile of the fused flip step (see k_fused.cu).  All threads of the CTA
 // call it; it synchronises the CTA internally and on return.
-// Site ownership of the flip: thread (warp, lane) owns, in each of four
-// passes j, the eight sites (row 8j + warp, columns 8 lane .. 8 lane + 7) of
-// the tile; their tile roots are one 16-byte word per pass.
+// Site ownership of the flip: with G = TILE_W / 8 column groups, thread k
+// owns, in each of four passes j, the eight sites (row 8j + k / G, columns
+// 8 (k % G) .. 8 (k % G) + 7) of the tile; their tile roots are one 16-byte
+// word per pass.
+constexpr int FLIP_GROUPS = TILE_W / 8;
 constexpr int FLIP_PASSES = TILE_SITES / (8 * LABEL_THREADS);
-static_assert(FLIP_PASSES * 8 * LABEL_THREADS == TILE_SITES && TILE_W == 256, "site ownership");
+static_assert(FLIP_PASSES * 8 * LABEL_THREADS == TILE_SITES && LABEL_THREADS / FLIP_GROUPS == 8, "site ownership");
 
 // Local root (16 bits) of site i (0..7) of a pass word.
 __device__ __forceinline__ int root_in(const uint4& v, int i) {
@@ -400,7 +402,7 @@ __device__ __forceinline__ void flip_tile_core(const SwRep& R, int t, uint64_t s
   const int y0 = ty * TILE_H, x0 = tx * TILE_W;
   const int h = min(TILE_H, L - y0), w = min(TILE_W, L - x0);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int lx0 = 8 * lane;
+  const int orow = threadIdx.x / FLIP_GROUPS, lx0 = 8 * (threadIdx.x % FLIP_GROUPS);   // my sites
   // the tile's edge-root bits, left by the labeling kernel
   fs.edge_bits[threadIdx.x] = (uint32_t)__ldcg(R.s.roots + (int64_t)t * TILE_SITES + threadIdx.x);
 
@@ -414,7 +416,7 @@ __device__ __forceinline__ void flip_tile_core(const SwRep& R, int t, uint64_t s
 #pragma unroll
   for (int j = 0; j < PASSES; ++j) {
     const uint4 rv = roots.get(j);
-    const uint32_t base = (uint32_t)((8 * j + warp) * TILE_W + lx0);
+    const uint32_t base = (uint32_t)((8 * j + orow) * TILE_W + lx0);
     const uint32_t own = base * 0x00010001u + 0x00010000u;   // (base, base + 1)
     const uint32_t wv[4] = {rv.x, rv.y, rv.z, rv.w};
 #pragma unroll
@@ -444,7 +446,7 @@ __device__ __forceinline__ void flip_tile_core(const SwRep& R, int t, uint64_t s
     const int b = __ffs(mine) - 1;
     mine &= mine - 1;
     const int jk = b & 15;
-    const int r = (8 * (jk >> 2) + warp) * TILE_W + lx0 + 2 * (jk & 3) + (b >> 4);
+    const int r = (8 * (jk >> 2) + orow) * TILE_W + lx0 + 2 * (jk & 3) + (b >> 4);
     rlist[base++] = (uint16_t)r | (((fs.edge_bits[r >> 5] >> (r & 31)) & 1u) ? EDGE_ROOT : (uint16_t)0);
   }
   __syncthreads();
@@ -489,7 +491,7 @@ __device__ __forceinline__ void flip_tile_core(const SwRep& R, int t, uint64_t s
   // 5. every site takes its tile root's state
 #pragma unroll
   for (int j = 0; j < PASSES; ++j) {
-    const int ly = 8 * j + warp;
+    const int ly = 8 * j + orow;
     if (ly >= h || lx0 + 4 > w) continue;
     const uint4 rv = roots.get(j);
     uint32_t lo = 0, hi = 0;
@@ -564,15 +566,14 @@ __device__ __forceinline__ void sw_flip_tile(const SwRep& R, int t, uint64_t swe
   const int ty = t / R.g.tiles_x, tx = t - ty * R.g.tiles_x;
   const int y0 = ty * TILE_H, x0 = tx * TILE_W;
   const int h = min(TILE_H, L - y0), w = min(TILE_W, L - x0);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int lx0 = 8 * lane;
+  const int orow = threadIdx.x / FLIP_GROUPS, lx0 = 8 * (threadIdx.x % FLIP_GROUPS);   // my sites
   // 1. tile roots of my sites (w is a multiple of 4: a group of eight sites is
   //    either wholly inside, or its first four are); read through L2 because a
   //    persistent kernel wrote them on other SMs
   RootsInRegs roots;
 #pragma unroll
   for (int j = 0; j < FLIP_PASSES; ++j) {
-    const int ly = 8 * j + warp;
+    const int ly = 8 * j + orow;
     const uint16_t* src = lroot + (int64_t)(y0 + ly) * L + x0 + lx0;
     uint4 v = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
     // 16-byte loads need L % 8 == 0; L % 4 == 0 always allows 8-byte loads

@@ -80,7 +80,7 @@ __device__ __forceinline__ bool grid_barrier(BatchCtl* ctl, unsigned nblocks, lo
 
 // ---------------------------------------------------------------------------
 // Phase kernels: one CTA per global tile (merge: one thread per seam bond).
-__global__ void __launch_bounds__(LABEL_THREADS, 5) k_batch_label(BatchView b, const BatchCtl* __restrict__ ctl) {
+__global__ void __launch_bounds__(LABEL_THREADS, LABEL_CTAS_PER_SM) k_batch_label(BatchView b, const BatchCtl* __restrict__ ctl) {
   __shared__ LabelTileSmem ls;
   const uint64_t sweep = ctl->sweep;
   const bool do_obs = batch_do_obs(ctl, sweep);
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(LABEL_THREADS, 5) k_batch_label(BatchView b, c
   sw_label_tile(R, gt - R.tile0, sweep, do_obs, b.obs_cap, ls, SeedKey{(uint32_t)R.seed, (uint32_t)(R.seed >> 32)});
 }
 
-constexpr int BATCH_MERGE_THREADS = 288;   // = MERGE_PER_TILE: one CTA per tile
+constexpr int BATCH_MERGE_THREADS = MERGE_PER_TILE;   // one CTA per tile
 
 __global__ void __launch_bounds__(BATCH_MERGE_THREADS) k_batch_merge(BatchView b) {
   const int gt = blockIdx.x;
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(BATCH_MERGE_THREADS) k_batch_merge(BatchView b
   merge_seam_bond(R.gpar, R.g, R.s, gt - R.tile0, threadIdx.x, true, b.limit);
 }
 
-__global__ void __launch_bounds__(LABEL_THREADS, 6) k_batch_flip(BatchView b, const BatchCtl* __restrict__ ctl) {
+__global__ void __launch_bounds__(LABEL_THREADS, FLIP_CTAS_PER_SM) k_batch_flip(BatchView b, const BatchCtl* __restrict__ ctl) {
   __shared__ FlipTileSmem fs;
   const int gt = blockIdx.x;
   const SwRep& R = b.reps[b.tile_rep[gt]];
@@ -122,7 +122,7 @@ union PersistentSmem {
   FlipTileSmem flip;
 };
 
-__global__ void __launch_bounds__(LABEL_THREADS, 4) k_batch_persistent(BatchView b, BatchCtl* ctl, long long limit_cycles) {
+__global__ void __launch_bounds__(LABEL_THREADS, 4 * 256 / TILE_W) k_batch_persistent(BatchView b, BatchCtl* ctl, long long limit_cycles) {
   __shared__ PersistentSmem u;
   const uint64_t sweep = ctl->sweep;
   const bool do_obs = batch_do_obs(ctl, sweep);

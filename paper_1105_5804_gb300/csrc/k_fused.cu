@@ -35,7 +35,7 @@
 namespace swccl {
 
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(LABEL_THREADS, 5)
+__global__ void __launch_bounds__(LABEL_THREADS, LABEL_CTAS_PER_SM)
 k_sw_label(SwRep R, const SwCtl* __restrict__ ctl, int obs_cap, const __grid_constant__ PhiloxKeys keys) {
   __shared__ LabelTileSmem ls;
   const uint64_t sweep = ctl->sweep;
@@ -43,13 +43,13 @@ k_sw_label(SwRep R, const SwCtl* __restrict__ ctl, int obs_cap, const __grid_con
   sw_label_tile(R, blockIdx.x, sweep, do_obs, obs_cap, ls, keys);
 }
 
-__global__ void __launch_bounds__(LABEL_THREADS, 6)
+__global__ void __launch_bounds__(LABEL_THREADS, FLIP_CTAS_PER_SM)
 k_sw_flip(SwRep R, const SwCtl* __restrict__ ctl, int limit, const __grid_constant__ PhiloxKeys keys) {
   __shared__ FlipTileSmem fs;
   sw_flip_tile(R, blockIdx.x, ctl->sweep, limit, fs, keys);
 }
 
-__global__ void __launch_bounds__(LABEL_THREADS, 6)
+__global__ void __launch_bounds__(LABEL_THREADS, FLIP_CTAS_PER_SM)
 k_sw_flip_few(SwRep R, const SwCtl* __restrict__ ctl, int limit, const uint32_t* __restrict__ sel, uint64_t P,
               const __grid_constant__ PhiloxKeys keys) {
   __shared__ FlipTileSmem fs;

@@ -15,11 +15,22 @@ enum : uint32_t { TAG_BOND = 0, TAG_FLIP = 1, TAG_INIT = 2, TAG_PERC = 3, TAG_SE
 
 // Tile of the local labeling phase: TILE_H rows x TILE_W columns, one CTA
 // per tile with one warp per 32-column strip (LABEL_THREADS = TILE_W).
-// TILE_W is a power of two and a multiple of 32; TILE_H a multiple of 32.
+// TILE_H = 32 (one lane per row of a strip); TILE_W is 64, 128 or 256.  The
+// library is built with TILE_W = 256; the batch libraries the autotuner
+// chooses from are built with SWCCL_TILE_W = 64 and 128 (narrower tiles
+// waste fewer threads on lattices that are not a multiple of 256 wide).
+#ifndef SWCCL_TILE_W
+#define SWCCL_TILE_W 256
+#endif
 constexpr int TILE_H = 32;
-constexpr int TILE_W = 256;
-constexpr int TILE_W_LOG2 = 8;
+constexpr int TILE_W = SWCCL_TILE_W;
+static_assert(TILE_W == 64 || TILE_W == 128 || TILE_W == 256, "tile width");
+constexpr int TILE_W_LOG2 = TILE_W == 64 ? 6 : TILE_W == 128 ? 7 : 8;
 constexpr int LABEL_THREADS = TILE_W;
+// Resident CTAs per SM the labeling and flip kernels are built for (the same
+// threads per SM at every tile width).
+constexpr int LABEL_CTAS_PER_SM = 5 * 256 / TILE_W;
+constexpr int FLIP_CTAS_PER_SM = 6 * 256 / TILE_W;
 
 // Per-tile seam record written by the local labeling phase and read by the
 // merge: labels of the four tile edges and the raw bond bits leaving the

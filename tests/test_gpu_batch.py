@@ -32,14 +32,18 @@ MIX = [  # (L, q, beta)
 ]
 
 
+@pytest.mark.parametrize("tile_w", [256, 128, 64])
 @pytest.mark.parametrize("schedule", [sw.SW_BATCH_PHASES, sw.SW_BATCH_PERSISTENT])
-def test_mixed_batch_matches_oracle(schedule):
+def test_mixed_batch_matches_oracle(schedule, tile_w):
+    """Every chain of a mixed batch (sizes from one ragged tile to several,
+    q = 2..5) equals the oracle's chain, for each labeling tile width the
+    autotuner can pick and both schedules."""
     conv = sw.SW_CONV_AUTO
     L = [m[0] for m in MIX]
     q = [m[1] for m in MIX]
     beta = [m[2] for m in MIX]
     seed = [1000 + 7 * r for r in range(len(MIX))]
-    b = sw.sw_batch_create(L, q, beta, seed, conv, True)
+    b = sw.sw_batch_create(L, q, beta, seed, conv, True, tile_w=tile_w)
     try:
         sw.sw_batch_set_schedule(b, schedule)
         spins = [oracle.init_spins(L[r], q[r], seed[r], True) for r in range(len(MIX))]
@@ -55,6 +59,7 @@ def test_mixed_batch_matches_oracle(schedule):
             done += n
         info = sw.sw_batch_info(b)
         assert info["chains"] == len(MIX) and info["sweeps"] == done and info["schedule"] == schedule
+        assert info["tile_w"] == tile_w
     finally:
         sw.sw_batch_destroy(b)
 
@@ -84,17 +89,19 @@ def test_512_replica_workload_sample_and_schedules_agree():
     q = [2] * 512
     b1 = sw.sw_batch_create(L, q, beta, seed, sw.SW_CONV_ISING, False)
     b2 = sw.sw_batch_create(L, q, beta, seed, sw.SW_CONV_ISING, False)
+    b3 = sw.sw_batch_create(L, q, beta, seed, sw.SW_CONV_ISING, False, tile_w=128)
+    b4 = sw.sw_batch_create(L, q, beta, seed, sw.SW_CONV_ISING, False, tile_w=64)
     try:
         sw.sw_batch_set_schedule(b2, sw.SW_BATCH_PERSISTENT)
-        sw.sw_batch_sweep(b1, 3)
-        sw.sw_batch_sweep(b2, 3)
+        for b in (b1, b2, b3, b4):
+            sw.sw_batch_sweep(b, 3)
         sample = sorted(range(512), key=lambda r: L[r])[:6] + [0, 255, 511]
         for r in range(512):
             s1 = sw.sw_batch_get_spins(b1, r, L[r])
-            s2 = sw.sw_batch_get_spins(b2, r, L[r])
-            assert np.array_equal(s1, s2), r
             o1 = sw.sw_batch_observables(b1, r, 2)
-            assert np.array_equal(o1, sw.sw_batch_observables(b2, r, 2)), r
+            for b in (b2, b3, b4):                # other schedule, other tile widths
+                assert np.array_equal(s1, sw.sw_batch_get_spins(b, r, L[r])), r
+                assert np.array_equal(o1, sw.sw_batch_observables(b, r, 2)), r
             assert np.all(o1[:, 1] + o1[:, 2] == L[r] * L[r])
             if r in sample:
                 T = _oracle_T(2, beta[r], oracle.CONV_ISING)
@@ -102,8 +109,27 @@ def test_512_replica_workload_sample_and_schedules_agree():
                 assert np.array_equal(s1, s), r
                 assert np.array_equal(o1, obs), r
     finally:
-        sw.sw_batch_destroy(b1)
-        sw.sw_batch_destroy(b2)
+        for b in (b1, b2, b3, b4):
+            sw.sw_batch_destroy(b)
+
+
+def test_autotuner_picks_a_tile_width_and_schedule_and_the_batch_matches_the_oracle(tmp_path, monkeypatch):
+    from paper_1105_5804_gb300 import autotune
+    monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "tune.json"))
+    L, q, beta, seed = [96, 160, 288, 64], [2, 2, 3, 2], [KC, 0.9 * KC, 0.8, 1.1 * KC], [21, 22, 23, 24]
+    b, choice = autotune.create_tuned(L, q, beta, seed, sw.SW_CONV_AUTO, True, sweeps=2, max_blocks_per_sm=2)
+    try:
+        assert choice["tile_w"] in (64, 128, 256) and len(choice["timings"]) == 3 * 3
+        assert sw.sw_batch_info(b)["tile_w"] == choice["tile_w"]
+        sw.sw_batch_sweep(b, 2)
+        sw.sw_batch_sync(b)
+        for r in range(len(L)):
+            T = _oracle_T(q[r], beta[r], oracle.CONV_AUTO)
+            s, obs = oracle.chain(L[r], q[r], T, seed[r], 0, 2, oracle.init_spins(L[r], q[r], seed[r], True))
+            assert np.array_equal(sw.sw_batch_get_spins(b, r, L[r]), s), r
+            assert np.array_equal(sw.sw_batch_observables(b, r, q[r]), obs), r
+    finally:
+        sw.sw_batch_destroy(b)
 
 
 def test_batch_rejects_bad_chains():
