@@ -29,20 +29,38 @@ L_BENCH, Q_BENCH, SEED_BENCH = 16384, 2, 7
 # self-labeling + sewing on a Tesla M2070, 3.573 ns per site and sweep (Table I)
 PAPER_SITE_UPDATES_PER_NS = 1.0 / 3.573
 WORKLOAD = "sw_ising_q2_L%d_beta_c_hot_start_seed7"
-# DRAM traffic of k_sw_label per site from one ncu capture at L = 8192 (the
-# full-size launch is too large to capture under ncu's replay; the traffic
-# grows with the sites processed): (dram__bytes_read.sum +
-# dram__bytes_write.sum) / sites = (99.45 + 167.47) MB / 67,108,864 (the ncu
-# capture of k_sw_label at L = 8192).  Valid only for the kernel
-# code it was taken with (label_sources_hash() below); otherwise the line
+# Counters of the fused sweep's kernels from one ncu capture each (--set
+# full, one launch, L = 8192, the third sweep from the hot start; the
+# full-size launch is too large to capture under ncu's replay, and DRAM
+# bytes and instructions grow with the sites processed), per site:
+# DRAM bytes = dram__bytes_read.sum + dram__bytes_write.sum, warp
+# instructions = smsp__inst_executed.sum.  Valid only for the code they were
+# taken with (a hash of the sources without comments); otherwise the line
 # reports null.
-LABEL_TRAFFIC_BYTES_PER_SITE = 3.977
-LABEL_TRAFFIC_SOURCES = ("fused_tile.cuh", "tile_engine.cuh", "k_fused.cu", "swccl_device.cuh", "swccl_shared.h")
-LABEL_TRAFFIC_SOURCE_HASH = "4e3a05ad73d002e9"
-
-
-def label_sources_hash():
-    return sources_hash(LABEL_TRAFFIC_SOURCES)
+SWEEP_COUNTER_SOURCES = ("fused_tile.cuh", "tile_engine.cuh", "k_fused.cu", "k_label.cu", "swccl_device.cuh",
+                         "swccl_shared.h")
+SWEEP_COUNTER_HASH = "c09620137f45deac"
+SWEEP_COUNTERS = {      # kernel: (DRAM bytes per site, warp instructions per site)
+    "k_sw_label": ((94.309120 + 141.168384) * 1e6 / 67108864, 191932390 / 67108864),
+    "k_merge": ((78.397952 + 2.257920) * 1e6 / 67108864, 15477841 / 67108864),
+    "k_sw_flip": ((216.637952 + 49.788672) * 1e6 / 67108864, 101021937 / 67108864),
+}
+# The stand-alone labeling call (k_ccl_tile, k_merge, k_ccl_final), one ncu
+# capture per kernel of a 4096^2 critical percolation mask: DRAM bytes per site.
+CCL_COUNTER_SOURCES = ("label_tile.cuh", "tile_engine.cuh", "k_label.cu", "swccl_device.cuh", "swccl_shared.h")
+CCL_COUNTER_HASH = "c58e6b4eb6f35421"
+CCL_TRAFFIC_BYTES_PER_SITE = ((4.294912 + 19.531008) + (16.797696 + 0.000256) + (74.642688 + 7.604736)) * 1e6 / 16777216
+# Algorithmic HBM bytes per site: the fused sweep reads and writes the int8
+# spins once (2 B, the minimum of any sweep); the kernel split adds the
+# 16-bit tile roots written by k_sw_label and read by k_sw_flip (6 B).
+SWEEP_MIN_BYTES_PER_SITE = 2.0
+FUSED_SWEEP_BYTES_PER_SITE = 6.0
+LABEL_BYTES_PER_SITE = 3.0      # k_sw_label: spins read 1 B, tile roots written 2 B
+# Philox4x32-10 calls per site made by k_sw_label: one call per pair of
+# x-adjacent sites (its four words are the pair's east and north bonds)
+LABEL_PHILOX_CALLS_PER_SITE = 0.5
+# sweeps of the separate pass that splits the sweep time by kernel
+PHASE_SWEEPS = 10
 
 
 def sources_hash(files):
@@ -60,33 +78,14 @@ def sources_hash(files):
     return h.hexdigest()[:16]
 
 
-# DRAM traffic of the stand-alone labeling call (its three kernels) per site,
-# from an ncu capture at 4096^2, valid for the code it was taken with.
-CCL_TRAFFIC_BYTES_PER_SITE = None
-CCL_TRAFFIC_SOURCES = ("label_tile.cuh", "tile_engine.cuh", "k_label.cu", "swccl_device.cuh", "swccl_shared.h")
-CCL_TRAFFIC_SOURCE_HASH = None
+def sweep_counters():
+    """Per-site (DRAM bytes, warp instructions) of the sweep's kernels, or
+    None if their code changed since the capture."""
+    return SWEEP_COUNTERS if sources_hash(SWEEP_COUNTER_SOURCES) == SWEEP_COUNTER_HASH else None
 
 
 def _ccl_traffic(N):
-    if CCL_TRAFFIC_BYTES_PER_SITE is None or sources_hash(CCL_TRAFFIC_SOURCES) != CCL_TRAFFIC_SOURCE_HASH:
-        return None
-    return CCL_TRAFFIC_BYTES_PER_SITE * N
-
-
-def _label_traffic(N):
-    """Per-launch DRAM bytes of k_sw_label scaled from the capture, or None
-    if the kernel's code changed since."""
-    return LABEL_TRAFFIC_BYTES_PER_SITE * N if label_sources_hash() == LABEL_TRAFFIC_SOURCE_HASH else None
-# Algorithmic HBM bytes per site of one fused sweep: k_sw_label reads the
-# int8 spins (1 B) and writes a 16-bit tile root (2 B); k_sw_flip reads the
-# root (2 B) and writes the spins (1 B).  Seam records and edge-root entries
-# (O(1/tile side)) are not counted.
-FUSED_SWEEP_BYTES_PER_SITE = 6.0
-# Philox4x32-10 calls per site made by k_sw_label: one call per pair of
-# x-adjacent sites (its four words are the pair's east and north bonds)
-LABEL_PHILOX_CALLS_PER_SITE = 0.5
-# sweeps of the separate pass that splits the sweep time by kernel
-PHASE_SWEEPS = 10
+    return CCL_TRAFFIC_BYTES_PER_SITE * N if sources_hash(CCL_COUNTER_SOURCES) == CCL_COUNTER_HASH else None
 
 
 def _peaks():
@@ -750,8 +749,57 @@ def run_ours(args):
     label_ms = per["local"]
     philox_peak = philox_ceiling(torch, sw)
     philox_achieved = LABEL_PHILOX_CALLS_PER_SITE * N / (label_ms * 1e-3)
-    hbm_achieved = FUSED_SWEEP_BYTES_PER_SITE * N / (ms_sweep * 1e-3) / 1e9
     mean_n_eq = float(obs[:, 0].mean()) if len(obs) else None
+    # issue-slot ceiling: every SM's four schedulers issue one warp
+    # instruction per cycle, at the SM clock sampled during the timed region
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sm_mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
+    issue_peak = props.multi_processor_count * 4 * sm_mhz * 1e6
+    counters = sweep_counters()
+    kernel_ms = {"k_sw_label": per["local"], "k_merge": per["merge"], "k_sw_flip": per["flip"]}
+
+    def hbm_gbs(bytes_per_site, t_ms):
+        return bytes_per_site * N / (t_ms * 1e-3) / 1e9
+
+    kernels = {}
+    for k, t in kernel_ms.items():
+        d = {"ms_per_launch": t}
+        if counters:
+            b, wi = counters[k]
+            d.update({"dram_bytes_per_site": b, "hbm_frac_measured": hbm_gbs(b, t) / peak_hbm,
+                      "warp_instructions_per_site": wi, "issue_frac": wi * N / (t * 1e-3) / issue_peak})
+        kernels[k] = d
+    roofline = {
+        "bound": "alu", "kernel": "k_sw_label", "unit": "G warp-instructions/s",
+        "achieved": counters["k_sw_label"][1] * N / (label_ms * 1e-3) / 1e9 if counters else None,
+        "peak": issue_peak / 1e9,
+        "frac": counters["k_sw_label"][1] * N / (label_ms * 1e-3) / issue_peak if counters else None,
+        "peak_kind": "derived: %d SMs x 4 schedulers x 1 warp instruction per cycle x %.0f MHz (median SM clock "
+                     "sampled in the timed region)" % (props.multi_processor_count, sm_mhz),
+        "work_model": "warp instructions per site (ncu smsp__inst_executed.sum of one launch at L=8192, per site) "
+                      "x %d sites per launch: the kernel is bound by instruction issue (Philox, bond logic, "
+                      "tile labeling), not by DRAM" % N,
+        "traffic": counters["k_sw_label"][0] * N if counters else None,
+        "traffic_note": "bytes per launch: ncu dram__bytes_read.sum + dram__bytes_write.sum per site at L=8192 "
+                        "x sites",
+        "ms_per_launch": label_ms,
+        "hbm_frac_algorithmic": hbm_gbs(LABEL_BYTES_PER_SITE, label_ms) / peak_hbm,
+        "hbm_frac_measured": hbm_gbs(counters["k_sw_label"][0], label_ms) / peak_hbm if counters else None,
+        "hbm_peak": peak_hbm, "hbm_peak_kind": peak_kind,
+        "philox": {"achieved_gcall_s": philox_achieved / 1e9, "ceiling_gcall_s": philox_peak / 1e9,
+                   "frac": philox_achieved / philox_peak,
+                   "ceiling_kind": "measured in this run: Philox-only kernel, 8 CTAs x 256 threads per SM"},
+    }
+    sweep_bytes = sum(v[0] for v in counters.values()) if counters else None
+    hbm_view = {
+        "unit": "GB/s", "peak": peak_hbm, "peak_kind": peak_kind, "ms_per_sweep": ms_sweep,
+        "measured_bytes_per_site": sweep_bytes,
+        "frac_measured": hbm_gbs(sweep_bytes, ms_sweep) / peak_hbm if counters else None,
+        "frac_at_2B_per_site": hbm_gbs(SWEEP_MIN_BYTES_PER_SITE, ms_sweep) / peak_hbm,
+        "frac_at_6B_per_site": hbm_gbs(FUSED_SWEEP_BYTES_PER_SITE, ms_sweep) / peak_hbm,
+        "models": "2 B/site: spins read and written once (any sweep's minimum); 6 B/site: plus the 16-bit tile "
+                  "roots k_sw_label writes and k_sw_flip reads; measured: the three kernels' ncu DRAM bytes",
+    }
     line = {
         "metric": "SW site-updates/ns", "value": value, "unit": "site-updates/ns", "n_gpus": world,
         "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps,
@@ -761,7 +809,9 @@ def run_ours(args):
         "config": {"workload": WORKLOAD % L, "L": L, "q": q, "beta": KC_ISING, "convention": "ising (K=2 beta J)",
                    "start": "hot", "seed": SEED_BENCH, "replicas": world, "parallelism": "replicas",
                    "l2": "inputs larger than L2 (spins %d MiB, 16-bit tile roots %d MiB per replica)"
-                         % (N >> 20, (2 * N) >> 20)},
+                         % (N >> 20, (2 * N) >> 20),
+                   "timed_path": "sw_sweep replaying one captured CUDA graph per sweep; the per-kernel split comes "
+                                 "from a separate pass of %d eagerly launched sweeps with events" % PHASE_SWEEPS},
         "clocks": clk,
         "gpu_launches": 4 * args.steps,
         "e2e": {"value": e2e_value, "unit": "site-updates/ns", "h2d_bytes_per_step": N,
@@ -771,18 +821,9 @@ def run_ours(args):
                         "buffers; spins up from and down to pinned host memory on two copy streams, double-buffered "
                         "(upload of step k+1 and download of step k-1 overlap step k); synchronous_value: the same "
                         "calls on the host buffers directly, one after another"},
-        "roofline": {"bound": "alu", "kernel": "k_sw_label", "achieved": philox_achieved / 1e9,
-                     "peak": philox_peak / 1e9, "unit": "Gcall/s (Philox4x32-10)",
-                     "frac": philox_achieved / philox_peak, "traffic": _label_traffic(N),
-                     "traffic_note": "bytes per launch: ncu dram read+write per site at L=8192 x sites",
-                     "peak_kind": "measured in this run: Philox-only kernel, 8 CTAs x 256 threads per SM",
-                     "work_model": "%.1f Philox calls/site x %d sites per launch; the kernel also labels its "
-                                   "tile, which shares the integer pipes" % (LABEL_PHILOX_CALLS_PER_SITE, N),
-                     "ms_per_launch": label_ms},
-        "hbm_view": {"bytes_per_site": FUSED_SWEEP_BYTES_PER_SITE, "achieved": hbm_achieved, "peak": peak_hbm,
-                     "unit": "GB/s", "frac": hbm_achieved / peak_hbm, "peak_kind": peak_kind,
-                     "model": "whole fused sweep: spins read 1 B + 16-bit roots written 2 B (k_sw_label), "
-                              "roots read 2 B + spins written 1 B (k_sw_flip)"},
+        "roofline": roofline,
+        "hbm_view": hbm_view,
+        "kernels": kernels,
         "phase_ms_per_sweep": per,
         "kernels_per_phase": {"local": "k_sw_label (bond draws + tile labeling)", "merge": "k_merge",
                               "flip": "k_sw_flip", "activate": "(fused into local)", "roots": "(fused into flip)"},
