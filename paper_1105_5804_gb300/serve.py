@@ -35,6 +35,8 @@ sw_observables, sw_destroy) on one stream, each finished before the next
 starts.
 """
 import collections
+import contextlib
+import gc
 import time
 
 import numpy as np
@@ -313,9 +315,29 @@ def make_jobs(rate, n_jobs, seed=0, label_fraction=0.8, hw=(256, 8192), sw_L=(12
     return jobs
 
 
+@contextlib.contextmanager
+def _no_collector_pauses():
+    """Python's cyclic garbage collector stops the loop for tens of
+    milliseconds when it scans a large heap; a serving loop keeps it off
+    (reference counting still frees every result) and runs it afterwards."""
+    was = gc.isenabled()
+    gc.collect()
+    gc.disable()
+    try:
+        yield
+    finally:
+        if was:
+            gc.enable()
+
+
 def run(jobs, server, time_scale=1.0):
     """Feed jobs at their arrival times (seconds from now x time_scale) and
     step the server until all are done.  Returns the completed jobs."""
+    with _no_collector_pauses():
+        return _run(jobs, server, time_scale)
+
+
+def _run(jobs, server, time_scale):
     torch = server.torch
     t0 = time.perf_counter()
     server.clock = lambda: time.perf_counter() - t0
@@ -339,6 +361,11 @@ def run_serial(jobs, stream=None, keep_results=False, pool=None):
     single-job calls on one stream and finished (result in host memory)
     before the next starts; a job that arrives while another runs waits.
     Returns the jobs with t_admit / t_done set (seconds from the start)."""
+    with _no_collector_pauses():
+        return _run_serial(jobs, stream, keep_results, pool)
+
+
+def _run_serial(jobs, stream, keep_results, pool):
     import torch
     st = stream or torch.cuda.Stream()
     pool = pool or pinned_pool()
