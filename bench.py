@@ -48,8 +48,8 @@ SWEEP_COUNTERS = {      # kernel: (DRAM bytes per site, warp instructions per si
 # The stand-alone labeling call (k_ccl_tile, k_merge, k_ccl_final), one ncu
 # capture per kernel of a 4096^2 critical percolation mask: DRAM bytes per site.
 CCL_COUNTER_SOURCES = ("label_tile.cuh", "tile_engine.cuh", "k_label.cu", "swccl_device.cuh", "swccl_shared.h")
-CCL_COUNTER_HASH = "c58e6b4eb6f35421"
-CCL_TRAFFIC_BYTES_PER_SITE = ((4.294912 + 19.531008) + (16.797696 + 0.000256) + (74.642688 + 7.604736)) * 1e6 / 16777216
+CCL_COUNTER_HASH = "ad371082e0dfa113"
+CCL_TRAFFIC_BYTES_PER_SITE = ((4.303104 + 20.025600) + (16.800256 + 0.000256) + (74.642432 + 8.067584)) * 1e6 / 16777216
 # Algorithmic HBM bytes per site: the fused sweep reads and writes the int8
 # spins once (2 B, the minimum of any sweep); the kernel split adds the
 # 16-bit tile roots written by k_sw_label and read by k_sw_flip (6 B).

@@ -29,8 +29,10 @@ __device__ __forceinline__ uint32_t even_bits(unsigned long long x) {
 // LOCAL (the stand-alone labeling path, finished by final_labels_tile): a
 // site that is not its tile's root gets -(r + 1), r its tile root's local
 // index, instead of the root's global index, and the root list holds local
-// indices.  Only tile roots' entries are global parent pointers, so the seam
-// merge and root lookups, which walk tile roots only, are unchanged.
+// indices, with CCL_EDGE_ROOT set on the roots whose component reaches the
+// tile edge.  Only tile roots' entries are global parent pointers, so the
+// seam merge and root lookups, which walk tile roots only, are unchanged.
+constexpr int CCL_EDGE_ROOT = 1 << 30;
 template <bool LOCAL = false>
 __device__ __forceinline__ void ccl_label_tile(const uint8_t* __restrict__ mask, int32_t* __restrict__ labels,
                                                const Grid& g, const LabelScratch& s, int t, TileSmem& sm) {
@@ -69,6 +71,29 @@ __device__ __forceinline__ void ccl_label_tile(const uint8_t* __restrict__ mask,
   // 2-4a. label the tile
   tile_engine(sm, h, slot, hook_log, s.err);
 
+  // LOCAL: mark the tile roots whose component reaches the tile edge (only
+  // they can belong to clusters that continue in other tiles); the marks go
+  // to the shared words the engine no longer needs
+  uint32_t* edge = reinterpret_cast<uint32_t*>(sm.pairs);
+  if (LOCAL) {
+    static_assert(TILE_SITES / 32 <= STRIPS * PAIR_FAST, "edge marks fit");
+    for (int k = threadIdx.x; k < TILE_SITES / 32; k += LABEL_THREADS) edge[k] = 0u;
+    __syncthreads();
+    auto mark = [&](int ly, int lx) {
+      const int r = par[par[ly * TILE_W + lx]];
+      atomicOr(&edge[r >> 5], 1u << (r & 31));
+    };
+    for (int k = threadIdx.x; k < h; k += LABEL_THREADS) {
+      mark(k, 0);
+      mark(k, w - 1);
+    }
+    for (int k = threadIdx.x; k < w; k += LABEL_THREADS) {
+      mark(0, k);
+      mark(h - 1, k);
+    }
+    __syncthreads();
+  }
+
   // 4b. every site's root; global labels; root list
   constexpr int PER_T = TILE_SITES / LABEL_THREADS;
   uint32_t mine = 0;      // bit j: site threadIdx.x + j*LABEL_THREADS is a root
@@ -104,7 +129,8 @@ __device__ __forceinline__ void ccl_label_tile(const uint8_t* __restrict__ mask,
     const int j = __ffs(mine) - 1;
     mine &= mine - 1;
     const int sidx = threadIdx.x + j * LABEL_THREADS;
-    slot[base++] = LOCAL ? sidx : (y0 + (sidx >> TILE_W_LOG2)) * W + x0 + (sidx & (TILE_W - 1));
+    slot[base++] = LOCAL ? (sidx | (((edge[sidx >> 5] >> (sidx & 31)) & 1u) ? CCL_EDGE_ROOT : 0))
+                         : (y0 + (sidx >> TILE_W_LOG2)) * W + x0 + (sidx & (TILE_W - 1));
   }
 
   // 5. seam record
@@ -180,7 +206,9 @@ __device__ __forceinline__ void final_labels_tile(int32_t* labels, const Grid& g
   const int h = min(TILE_H, g.H - y0), w = min(TILE_W, g.W - x0);
   const int n = __ldcg(s.root_counts + t);
   const int32_t* list = s.roots + (int64_t)t * TILE_SITES;
-  // 1. cluster roots of the tile roots, four walks of a thread in flight together
+  // 1. cluster roots of the tile roots: a root whose component stays inside
+  //    the tile is its cluster's root; the others walk the label array, four
+  //    walks of a thread in flight together
   constexpr int U = 4;
   for (int k0 = threadIdx.x; k0 < n; k0 += U * (int)blockDim.x) {
     int r[U], x[U];
@@ -188,14 +216,15 @@ __device__ __forceinline__ void final_labels_tile(int32_t* labels, const Grid& g
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int k = k0 + u * (int)blockDim.x;
-      act[u] = k < n;
-      r[u] = act[u] ? __ldcg(list + k) : 0;   // local index
+      const int raw = k < n ? __ldcg(list + k) : 0;
+      r[u] = raw & ~CCL_EDGE_ROOT;   // local index
+      act[u] = k < n && (raw & CCL_EDGE_ROOT);
       x[u] = tile_global(r[u], y0, x0, g.W);
     }
     g_find_multi<U>(labels, x, act, limit, s.err);
 #pragma unroll
     for (int u = 0; u < U; ++u)
-      if (act[u]) table[r[u]] = x[u];
+      if (k0 + u * (int)blockDim.x < n) table[r[u]] = x[u];
   }
   __syncthreads();
   // 2. every site takes its tile root's cluster root: four sites per 16-byte
