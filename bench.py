@@ -39,11 +39,11 @@ WORKLOAD = "sw_ising_q2_L%d_beta_c_hot_start_seed7"
 # reports null.
 SWEEP_COUNTER_SOURCES = ("fused_tile.cuh", "tile_engine.cuh", "k_fused.cu", "k_label.cu", "swccl_device.cuh",
                          "swccl_shared.h")
-SWEEP_COUNTER_HASH = "c09620137f45deac"
+SWEEP_COUNTER_HASH = "7da8cd6feffe39bf"
 SWEEP_COUNTERS = {      # kernel: (DRAM bytes per site, warp instructions per site)
-    "k_sw_label": ((94.309120 + 141.168384) * 1e6 / 67108864, 191932390 / 67108864),
-    "k_merge": ((78.397952 + 2.257920) * 1e6 / 67108864, 15477841 / 67108864),
-    "k_sw_flip": ((216.637952 + 49.788672) * 1e6 / 67108864, 101021937 / 67108864),
+    "k_sw_label": ((94.248960 + 141.197568) * 1e6 / 67108864, 191931469 / 67108864),
+    "k_merge": ((78.399488 + 2.282240) * 1e6 / 67108864, 15480206 / 67108864),
+    "k_sw_flip": ((216.624128 + 49.625856) * 1e6 / 67108864, 88897500 / 67108864),
 }
 # The stand-alone labeling call (k_ccl_tile, k_merge, k_ccl_final), one ncu
 # capture per kernel of a 4096^2 critical percolation mask: DRAM bytes per site.

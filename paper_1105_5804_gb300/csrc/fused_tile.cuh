@@ -594,6 +594,111 @@ __device__ __forceinline__ void sw_flip_tile(const SwRep& R, int t, uint64_t swe
   flip_tile_core<FEW>(R, t, sweep, limit, fs, roots, sel, P, keys);
 }
 
+// The flip of tile t when every tile of the lattice is whole (L a multiple
+// of TILE_W, TILE_H and 8): the steps of flip_tile_core with no bounds
+// checks, and the tile roots of the calling thread's sites read through L2
+// twice (root discovery, site pass) instead of held in registers across
+// the draws, which would not fit the register budget of six CTAs per SM.
+template <class Keys>
+__device__ __forceinline__ void sw_flip_whole_tile(const SwRep& R, int t, uint64_t sweep, int limit,
+                                                   FlipTileSmem& fs, const Keys& keys) {
+  constexpr int PASSES = FLIP_PASSES;
+  const int L = R.g.W;
+  const int ty = t / R.g.tiles_x, tx = t - ty * R.g.tiles_x;
+  const int y0 = ty * TILE_H, x0 = tx * TILE_W;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int orow = threadIdx.x / FLIP_GROUPS, lx0 = 8 * (threadIdx.x % FLIP_GROUPS);   // my sites
+  const uint16_t* src0 = R.lroot + (int64_t)(y0 + orow) * L + x0 + lx0;   // pass 0; 16-byte aligned
+  const int64_t pass_stride = (int64_t)8 * L;
+  uint16_t* rlist = fs.rlist;
+  uint8_t* ns = fs.ns;
+  int* warp_cnt = fs.warp_cnt;
+  fs.edge_bits[threadIdx.x] = (uint32_t)__ldcg(R.s.roots + (int64_t)t * TILE_SITES + threadIdx.x);
+
+  // 2. my roots (as in flip_tile_core)
+  uint32_t mine = 0;
+  {
+    uint4 held[PASSES];
+#pragma unroll
+    for (int j = 0; j < PASSES; ++j) held[j] = __ldcg(reinterpret_cast<const uint4*>(src0 + j * pass_stride));
+#pragma unroll
+    for (int j = 0; j < PASSES; ++j) {
+      const uint4 rv = held[j];
+      const uint32_t base = (uint32_t)((8 * j + orow) * TILE_W + lx0);
+      const uint32_t own = base * 0x00010001u + 0x00010000u;
+      const uint32_t wv[4] = {rv.x, rv.y, rv.z, rv.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t x = wv[k] ^ (own + (uint32_t)k * 0x00020002u);
+        const uint32_t nz = ((x & 0x7FFF7FFFu) + 0x7FFF7FFFu) | x;
+        mine |= (~nz & 0x80008000u) >> (15 - (4 * j + k));
+      }
+    }
+  }
+  const int cnt = __popc(mine);
+  int incl = cnt;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int v = __shfl_up_sync(FULL, incl, d);
+    if (lane >= d) incl += v;
+  }
+  if (lane == 31) warp_cnt[warp] = incl;
+  __syncthreads();
+  int base = 0, n_roots = 0;
+#pragma unroll
+  for (int k = 0; k < LABEL_THREADS / 32; ++k) {
+    base += (k < warp) ? warp_cnt[k] : 0;
+    n_roots += warp_cnt[k];
+  }
+  base += incl - cnt;
+  while (mine) {   // 3. the tile's root list, edge roots flagged
+    const int b = __ffs(mine) - 1;
+    mine &= mine - 1;
+    const int jk = b & 15;
+    const int r = (8 * (jk >> 2) + orow) * TILE_W + lx0 + 2 * (jk & 3) + (b >> 4);
+    rlist[base++] = (uint16_t)r | (((fs.edge_bits[r >> 5] >> (r & 31)) & 1u) ? EDGE_ROOT : (uint16_t)0);
+  }
+  __syncthreads();
+
+  // 4. one draw per tile root, keyed by its cluster's final root
+  constexpr int U = 2;
+  for (int k0 = threadIdx.x; k0 < n_roots; k0 += U * LABEL_THREADS) {
+    int r[U], Rg[U];
+    bool act[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int k = k0 + u * LABEL_THREADS;
+      const int raw = k < n_roots ? (int)rlist[k] : 0;
+      r[u] = raw & ROOT_MASK;
+      Rg[u] = tile_global(r[u], y0, x0, L);
+      act[u] = k < n_roots && (raw & EDGE_ROOT);
+    }
+    g_find_multi<U>(R.gpar, Rg, act, limit, R.s.err);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (k0 + u * LABEL_THREADS >= n_roots) break;
+      const uint4 d =
+          philox_draw(make_uint4((uint32_t)Rg[u], (uint32_t)sweep, (uint32_t)(sweep >> 32), TAG_FLIP), keys);
+      ns[r[u]] = (uint8_t)state_of(d.x, R.q);
+    }
+  }
+  __syncthreads();
+
+  // 5. every site takes its tile root's state (tile roots read again)
+#pragma unroll
+  for (int j = 0; j < PASSES; ++j) {
+    const int ly = 8 * j + orow;
+    const uint4 rv = __ldcg(reinterpret_cast<const uint4*>(src0 + j * pass_stride));
+    uint32_t lo = 0, hi = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) lo |= (uint32_t)ns[root_in(rv, i)] << (8 * i);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) hi |= (uint32_t)ns[root_in(rv, 4 + i)] << (8 * i);
+    int8_t* dst = R.spins + (int64_t)(y0 + ly) * L + x0 + lx0;
+    *reinterpret_cast<uint2*>(dst) = make_uint2(lo, hi);   // 8-byte aligned: L % 8 == 0
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Few-cluster seed selection (Sec. III, variant (c)): the seed of block b of
 // the ell x ell block grid (side B = L / ell) is (bx B + F_B(w.x),

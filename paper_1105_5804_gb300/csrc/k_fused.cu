@@ -49,6 +49,13 @@ k_sw_flip(SwRep R, const SwCtl* __restrict__ ctl, int limit, const __grid_consta
   sw_flip_tile(R, blockIdx.x, ctl->sweep, limit, fs, keys);
 }
 
+// k_sw_flip when every tile of the lattice is whole (selected on the host).
+__global__ void __launch_bounds__(LABEL_THREADS, FLIP_CTAS_PER_SM)
+k_sw_flip_whole(SwRep R, const SwCtl* __restrict__ ctl, int limit, const __grid_constant__ PhiloxKeys keys) {
+  __shared__ FlipTileSmem fs;
+  sw_flip_whole_tile(R, blockIdx.x, ctl->sweep, limit, fs, keys);
+}
+
 __global__ void __launch_bounds__(LABEL_THREADS, FLIP_CTAS_PER_SM)
 k_sw_flip_few(SwRep R, const SwCtl* __restrict__ ctl, int limit, const uint32_t* __restrict__ sel, uint64_t P,
               const __grid_constant__ PhiloxKeys keys) {
@@ -148,7 +155,10 @@ cudaError_t launch_sw_flip(int8_t* spins, const uint16_t* lroot, int32_t* gpar, 
                            const LabelScratch& s, int q, uint64_t seed, const SwCtl* ctl, cudaStream_t st) {
   const int limit = (int)std::min<int64_t>(g.n_sites() + 64, (int64_t)1 << 30);
   const SwRep R = make_rep(spins, const_cast<uint16_t*>(lroot), gpar, nullptr, g, s, q, 0, seed);
-  k_sw_flip<<<g.n_tiles(), LABEL_THREADS, 0, st>>>(R, ctl, limit, philox_keys(seed));
+  if (g.W % TILE_W == 0 && g.H % TILE_H == 0 && g.W % 8 == 0)   // every tile whole
+    k_sw_flip_whole<<<g.n_tiles(), LABEL_THREADS, 0, st>>>(R, ctl, limit, philox_keys(seed));
+  else
+    k_sw_flip<<<g.n_tiles(), LABEL_THREADS, 0, st>>>(R, ctl, limit, philox_keys(seed));
   return cudaGetLastError();
 }
 

@@ -49,7 +49,8 @@ def _run_few(L, q, T, P, ell, seed, n_sweeps, per_call=3, timing=False):
 
 @pytest.mark.parametrize("P", [HALF, FULL])
 @pytest.mark.parametrize("q", [2, 3])
-@pytest.mark.parametrize("L,ells", [(36, (1, 3, 36)), (100, (2, 25, 100)), (260, (1, 13, 65)), (292, (4, 73, 292))])
+@pytest.mark.parametrize("L,ells", [(36, (1, 3, 36)), (100, (2, 25, 100)), (256, (1, 16, 256)), (260, (1, 13, 65)),
+                                    (292, (4, 73, 292))])
 def test_few_cluster_chains(L, ells, q, P):
     for ell in ells:
         _run_few(L, q, _T(q), P, ell, seed=500 + L + q + ell, n_sweeps=8)

@@ -230,7 +230,8 @@ def test_fused_ising_L64_cold_start_1000_sweeps():
     _run_fused(L, q, T, seed, False, 1000, per_call=50)
 
 
-@pytest.mark.parametrize("L", [4, 8, 36, 100, 132, 196, 260, 292])
+# 256 and 512: every tile whole (the kernels without bounds checks)
+@pytest.mark.parametrize("L", [4, 8, 36, 100, 132, 196, 256, 260, 292, 512])
 @pytest.mark.parametrize("q", [2, 3, 4])
 def test_fused_small_lattices(L, q):
     beta = math.log(1 + math.sqrt(q))
@@ -238,10 +239,11 @@ def test_fused_small_lattices(L, q):
     _run_fused(L, q, T, seed=2000 + L + q, hot=True, n_sweeps=8, per_call=3)
 
 
+@pytest.mark.parametrize("L", [256, 260])
 @pytest.mark.parametrize("q", [5, 9, 127])
-def test_fused_many_states(q):
+def test_fused_many_states(L, q):
     T = oracle.threshold(oracle.coupling_K(q, math.log(1 + math.sqrt(q)), 1.0, oracle.CONV_POTTS))
-    _run_fused(260, q, T, seed=8, hot=True, n_sweeps=5)
+    _run_fused(L, q, T, seed=8, hot=True, n_sweeps=5)
 
 
 @pytest.mark.parametrize("T", [0, 1, 1 << 31, (1 << 32) - 1, 1 << 32])
@@ -275,9 +277,10 @@ def test_fused_timed_mode_several_sweeps_per_call():
 
 
 # Calls of 1 to 6 fused sweeps on lattices of one tile that is its own east
-# and north neighbour (L = 4, 8), ragged tiles (36, 260, 292) and several
-# ragged tiles each way (516); q = 127 counts the states one by one.
-@pytest.mark.parametrize("L", [4, 8, 36, 260, 292, 516])
+# and north neighbour (L = 4, 8), ragged tiles (36, 260, 292), several
+# ragged tiles each way (516) and whole tiles only (512); q = 127 counts the
+# states one by one.
+@pytest.mark.parametrize("L", [4, 8, 36, 260, 292, 512, 516])
 @pytest.mark.parametrize("q", [2, 3, 127])
 def test_fused_calls_of_several_sweeps(L, q):
     beta = math.log(1 + math.sqrt(q))

@@ -45,7 +45,7 @@ def _chain(L, q, ratio, seed, n_sweeps, mode, per_call):
 
 @pytest.mark.parametrize("ratio", [0.6, 1.4])
 @pytest.mark.parametrize("q", [2, 3])
-@pytest.mark.parametrize("L", [36, 260])
+@pytest.mark.parametrize("L", [36, 256, 260])
 def test_fused_chain_off_critical(L, q, ratio):
     s = _chain(L, q, ratio, seed=300 + L + q, n_sweeps=40, mode=sw.SW_MODE_FUSED, per_call=10)
     if ratio == 1.4 and q == 2:
