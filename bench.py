@@ -39,17 +39,17 @@ WORKLOAD = "sw_ising_q2_L%d_beta_c_hot_start_seed7"
 # reports null.
 SWEEP_COUNTER_SOURCES = ("fused_tile.cuh", "tile_engine.cuh", "k_fused.cu", "k_label.cu", "swccl_device.cuh",
                          "swccl_shared.h")
-SWEEP_COUNTER_HASH = "7da8cd6feffe39bf"
+SWEEP_COUNTER_HASH = "29dc69aefe68f8b0"
 SWEEP_COUNTERS = {      # kernel: (DRAM bytes per site, warp instructions per site)
-    "k_sw_label": ((94.248960 + 141.197568) * 1e6 / 67108864, 191931469 / 67108864),
-    "k_merge": ((78.399488 + 2.282240) * 1e6 / 67108864, 15480206 / 67108864),
-    "k_sw_flip": ((216.624128 + 49.625856) * 1e6 / 67108864, 88897500 / 67108864),
+    "k_sw_label": ((94.317056 + 141.447168) * 1e6 / 67108864, 187235547 / 67108864),
+    "k_merge": ((78.398976 + 2.100224) * 1e6 / 67108864, 15475005 / 67108864),
+    "k_sw_flip": ((216.697600 + 49.599232) * 1e6 / 67108864, 88898788 / 67108864),
 }
 # The stand-alone labeling call (k_ccl_tile, k_merge, k_ccl_final), one ncu
 # capture per kernel of a 4096^2 critical percolation mask: DRAM bytes per site.
 CCL_COUNTER_SOURCES = ("label_tile.cuh", "tile_engine.cuh", "k_label.cu", "swccl_device.cuh", "swccl_shared.h")
-CCL_COUNTER_HASH = "ad371082e0dfa113"
-CCL_TRAFFIC_BYTES_PER_SITE = ((4.303104 + 20.025600) + (16.800256 + 0.000256) + (74.642432 + 8.067584)) * 1e6 / 16777216
+CCL_COUNTER_HASH = "f484848673f87f5c"
+CCL_TRAFFIC_BYTES_PER_SITE = ((4.294912 + 19.587840) + (16.799232 + 0.000768) + (74.641408 + 8.061952)) * 1e6 / 16777216
 # Algorithmic HBM bytes per site: the fused sweep reads and writes the int8
 # spins once (2 B, the minimum of any sweep); the kernel split adds the
 # 16-bit tile roots written by k_sw_label and read by k_sw_flip (6 B).

@@ -294,29 +294,19 @@ __device__ __forceinline__ void sw_label_tile(const SwRep& R, int t, uint64_t sw
     observables_commit<LABEL_THREADS>(q, q <= QREG ? q : 0, oslot, red, hist);
   }
 
-  // 3. tile roots as 16-bit local indices, eight sites per thread and store
+  // 3. tile roots as 16-bit local indices: per step a thread takes four
+  //    consecutive sites (consecutive lanes, consecutive 16-byte words of
+  //    par: no bank conflicts) and stores 8 bytes (L % 4 == 0; w is a
+  //    multiple of 4, so four sites are all inside or all outside)
   auto entry = [&](int p) -> uint32_t { return (uint32_t)sm.par[p]; };   // p = par[site]
-  for (int k = threadIdx.x; k < TILE_SITES / 8; k += LABEL_THREADS) {
-    const int sidx = 8 * k;
+#pragma unroll 2
+  for (int k = threadIdx.x; k < TILE_SITES / 4; k += LABEL_THREADS) {
+    const int sidx = 4 * k;
     const int ly = sidx >> TILE_W_LOG2, lx = sidx & (TILE_W - 1);
-    if (ly >= h || lx >= w) continue;   // w is a multiple of 4: the first four sites are inside
+    if (ly >= h || lx >= w) continue;
     const int4 pa = *reinterpret_cast<const int4*>(&sm.par[sidx]);
-    const uint2 lo = make_uint2(entry(pa.x) | (entry(pa.y) << 16),
-                                entry(pa.z) | (entry(pa.w) << 16));
     uint16_t* dst = lroot + (int64_t)(y0 + ly) * L + x0 + lx;
-    if (lx + 8 <= w) {
-      const int4 pb = *reinterpret_cast<const int4*>(&sm.par[sidx + 4]);
-      const uint2 hi = make_uint2(entry(pb.x) | (entry(pb.y) << 16),
-                                  entry(pb.z) | (entry(pb.w) << 16));
-      if ((L & 7) == 0) {   // row starts 16-byte aligned
-        *reinterpret_cast<uint4*>(dst) = make_uint4(lo.x, lo.y, hi.x, hi.y);
-      } else {              // L % 4 == 0: 8-byte aligned
-        *reinterpret_cast<uint2*>(dst) = lo;
-        *reinterpret_cast<uint2*>(dst + 4) = hi;
-      }
-    } else {
-      *reinterpret_cast<uint2*>(dst) = lo;
-    }
+    *reinterpret_cast<uint2*>(dst) = make_uint2(entry(pa.x) | (entry(pa.y) << 16), entry(pa.z) | (entry(pa.w) << 16));
   }
 
   // 4. seam record; parent entries of edge roots; edge roots marked

@@ -29,9 +29,9 @@
 //     unreached run); the anchor lane's candidate -- the label below it if it
 //     is a first contact, else its own index -- is the run's label (one
 //     shuffle).  No union-find work happens in the sweep.
-//  3. the extra contacts whose two labels differ are listed per warp and
-//     joined with the shared-memory union-find (larger root hooked under the
-//     smaller), and so are the east bonds from strip c into strip c + 1;
+//  3. the extra contacts whose two labels differ, and the east bonds from
+//     strip c into strip c + 1, are listed per warp and joined with the
+//     shared-memory union-find (larger root hooked under the smaller);
 //     hooked roots are logged;
 //  4. logged roots resolve their final roots, so every node points at its
 //     root and every site's label (a node) is one step from it.
@@ -50,7 +50,10 @@ constexpr int STRIPS = TILE_W / 32;
 static_assert(LABEL_THREADS == TILE_W, "one warp per 32-column strip");
 static_assert(TILE_H == 32, "one lane per row of a strip");
 constexpr unsigned FULL = 0xFFFFFFFFu;
-constexpr int PAIR_CAP = TILE_SITES / STRIPS;   // per warp: at most 32 extra contacts per row word
+// Per warp at most 32 pairs per row word: a run's first contact is no extra
+// contact, so a row word of r runs has at most 32 - r <= 31, plus the
+// strip join.
+constexpr int PAIR_CAP = TILE_SITES / STRIPS;
 // Lists kept in shared memory up to these lengths, the rest in global scratch.
 constexpr int PAIR_FAST = 4 * TILE_H;           // per warp (the space of the sweep inputs)
 constexpr int HOOK_FAST = 512;
@@ -153,10 +156,10 @@ __device__ __forceinline__ void tile_engine_regs(TileSmem& sm, uint32_t we, uint
   __syncthreads();
 
   // 3. joins.  The extra contacts of my row (lane = row) whose two labels
-  //    differ are listed in the warp's part of `pairs` (a contact whose
-  //    runs already carry one label joins nothing new), then the warp joins
-  //    its list 32 pairs at a time; and the east bonds from strip c into
-  //    strip c + 1 (one row per lane).
+  //    differ (a contact whose runs already carry one label joins nothing
+  //    new), and the east bond of my row from strip c into strip c + 1, are
+  //    listed in the warp's part of `pairs`; then the warp joins its list 32
+  //    pairs at a time.
   {
     const uint32_t* be = sm.be;
     const uint32_t* bn = sm.bn;
@@ -166,20 +169,36 @@ __device__ __forceinline__ void tile_engine_regs(TileSmem& sm, uint32_t we, uint
       const int b = __ffs(x) - 1;
       if (par[row + b] != par[row - TILE_W + b]) D |= 1u << b;
     }
-    const int cnt = __popc(D);
+    bool join = false;   // east bond into the next strip, unless joined below
+    if (warp < STRIPS - 1 && lane < h) {
+      const int ly = lane, c = warp;
+      join = (be[ly * STRIPS + c] >> 31) & 1u;
+      if (join && ly > 0) {
+        const int k0 = (ly - 1) * STRIPS + c;
+        if (((be[k0] >> 31) & 1u) && ((bn[k0] >> 31) & 1u) && (bn[k0 + 1] & 1u)) join = false;
+      }
+    }
+    const int cnt = __popc(D) + (join ? 1 : 0);
     int incl = cnt;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
       const int v = __shfl_up_sync(FULL, incl, d);
       if (lane >= d) incl += v;
     }
-    const int total = __shfl_sync(FULL, incl, 31);
+    const int total = __shfl_sync(FULL, incl, 31);   // at most PAIR_CAP
     int* fast = sm.pairs + warp * PAIR_FAST;
     int32_t* slow = pairs + warp * PAIR_CAP;
     __syncwarp();                                 // the warp's sweep inputs are read
-    for (int k = incl - cnt; D; D &= D - 1, ++k) {
+    int k = incl - cnt;
+    for (; D; D &= D - 1, ++k) {
       const int b = __ffs(D) - 1;
       const int v = (par[row + b] << 16) | par[row - TILE_W + b];
+      if (k < PAIR_FAST) fast[k] = v;
+      else slow[k - PAIR_FAST] = v;
+    }
+    if (join) {
+      const int a = row + 31;   // last column of strip c, row `lane`
+      const int v = (par[a] << 16) | par[a + 1];
       if (k < PAIR_FAST) fast[k] = v;
       else slow[k - PAIR_FAST] = v;
     }
@@ -188,18 +207,6 @@ __device__ __forceinline__ void tile_engine_regs(TileSmem& sm, uint32_t we, uint
       const int v = j < PAIR_FAST ? fast[j] : slow[j - PAIR_FAST];
       sm_union_log(par, v >> 16, v & 0xFFFF, TILE_SITES, err, sm.hooks, HOOK_FAST, hook_log, &sm.n_hooked,
                    TILE_SITES);
-    }
-    if (warp < STRIPS - 1 && lane < h) {
-      const int ly = lane, c = warp;
-      bool join = (be[ly * STRIPS + c] >> 31) & 1u;
-      if (join && ly > 0) {
-        const int k0 = (ly - 1) * STRIPS + c;
-        if (((be[k0] >> 31) & 1u) && ((bn[k0] >> 31) & 1u) && (bn[k0 + 1] & 1u)) join = false;   // joined below
-      }
-      if (join) {
-        const int a = ly * TILE_W + c * 32 + 31;
-        sm_union_log(par, a, a + 1, TILE_SITES, err, sm.hooks, HOOK_FAST, hook_log, &sm.n_hooked, TILE_SITES);
-      }
     }
   }
   __syncthreads();

@@ -71,16 +71,19 @@ def test_few_cluster_timed_mode():
     _run_few(260, 2, _T(2), HALF, 5, seed=12, n_sweeps=6, per_call=1, timing=True)
 
 
-def test_switching_between_sw_and_few_cluster():
-    L, q, seed = 260, 3, 71
+# L = 256: the SW sweeps go through the site codes, the few-cluster sweeps
+# through the 16-bit tile roots
+@pytest.mark.parametrize("L,e1,e2", [(260, 5, 13), (256, 4, 16)])
+def test_switching_between_sw_and_few_cluster(L, e1, e2):
+    q, seed = 3, 71
     T = _T(q)
     h = sw.sw_create_threshold(L, q, T, seed, True)
     try:
         s = oracle.init_spins(L, q, seed, True)
         done = 0
-        for upd, ell, P, n in [(sw.SW_UPDATE_SW, 0, 0, 3), (sw.SW_UPDATE_FEW, 5, HALF, 4),
-                               (sw.SW_UPDATE_FEW, 13, FULL, 2), (sw.SW_UPDATE_SW, 0, 0, 2),
-                               (sw.SW_UPDATE_FEW, 5, HALF, 3)]:
+        for upd, ell, P, n in [(sw.SW_UPDATE_SW, 0, 0, 3), (sw.SW_UPDATE_FEW, e1, HALF, 4),
+                               (sw.SW_UPDATE_FEW, e2, FULL, 2), (sw.SW_UPDATE_SW, 0, 0, 2),
+                               (sw.SW_UPDATE_FEW, e1, HALF, 3)]:
             sw.sw_set_update(h, upd, ell, P)
             sw.sw_sweep(h, n)
             if upd == sw.SW_UPDATE_SW:

@@ -246,15 +246,19 @@ def test_fused_many_states(L, q):
     _run_fused(L, q, T, seed=8, hot=True, n_sweeps=5)
 
 
+# L = 256 with T = 0: every site its own cluster, so every tile has more
+# edge roots than code slots
 @pytest.mark.parametrize("T", [0, 1, 1 << 31, (1 << 32) - 1, 1 << 32])
 @pytest.mark.parametrize("per_call", [1, 4])
-def test_fused_degenerate_thresholds(T, per_call):
-    _run_fused(68, 2, T, seed=3, hot=True, n_sweeps=8, per_call=per_call)
+@pytest.mark.parametrize("L", [68, 256])
+def test_fused_degenerate_thresholds(L, T, per_call):
+    _run_fused(L, 2, T, seed=3, hot=True, n_sweeps=8, per_call=per_call)
 
 
-def test_fused_timed_mode_and_one_sweep_per_call():
+@pytest.mark.parametrize("L", [292, 512])
+def test_fused_timed_mode_and_one_sweep_per_call(L):
     T = oracle.threshold(oracle.coupling_K(2, KC, 1.0, oracle.CONV_ISING))
-    _run_fused(292, 2, T, seed=12, hot=True, n_sweeps=6, timing=True)
+    _run_fused(L, 2, T, seed=12, hot=True, n_sweeps=6, timing=True)
 
 
 def test_fused_timed_mode_several_sweeps_per_call():
@@ -300,10 +304,12 @@ def test_fused_calls_of_several_sweeps(L, q):
         sw.sw_destroy(h)
 
 
-def test_mode_switches_keep_the_chain():
+@pytest.mark.parametrize("L", [256, 260])
+def test_mode_switches_keep_the_chain(L):
     """staged -> fused -> staged -> fused within one chain, with reads of the
-    observables at every switch and in between."""
-    L, q, seed = 260, 3, 44
+    observables at every switch and in between (L = 256: the fused sweeps
+    go through the site codes)."""
+    q, seed = 3, 44
     T = oracle.threshold(oracle.coupling_K(q, math.log(1 + math.sqrt(3)), 1.0, oracle.CONV_POTTS))
     h = sw.sw_create_threshold(L, q, T, seed, True)
     try:
