@@ -112,8 +112,11 @@ def pinned_pool(arena_bytes=12 << 30):
     return _POOLS[arena_bytes]
 
 
+MAX_GROUP_WORK = 32 << 20         # pixels or site updates of one group (one job may exceed it)
+
+
 class Job:
-    __slots__ = ("id", "kind", "arrival", "H", "W", "pixels", "L", "beta", "sweeps", "seed", "bytes",
+    __slots__ = ("id", "kind", "arrival", "H", "W", "pixels", "L", "beta", "sweeps", "seed", "bytes", "work",
                  "t_admit", "t_done", "labels", "observables", "spins", "host_buf")
 
     def __init__(self, jid, kind, arrival, **kw):
@@ -127,7 +130,9 @@ class Job:
         self.seed = kw.get("seed", jid)
         if kind == "label":
             self.bytes = int(self.H * self.W * LABEL_BYTES_PER_PX) + sw.ccl_batch_workspace_bytes([self.H], [self.W])
+            self.work = self.H * self.W
         else:
+            self.work = self.L * self.L * self.sweeps
             # what a batch of this one chain allocates (a group's batch takes the
             # sum of its chains' shares and one set of small tables)
             self.bytes = sw.sw_batch_device_bytes([self.L], [2])
@@ -146,11 +151,16 @@ class _Group:
 
 
 class Server:
-    def __init__(self, hbm_budget_bytes, slots=4, max_group=32, keep_results=False, pool=None, streams=None):
+    def __init__(self, hbm_budget_bytes, slots=4, max_group=32, keep_results=False, pool=None, streams=None,
+                 max_group_work=MAX_GROUP_WORK):
         """streams: the slots' CUDA streams (default: new ones).  A process
         that runs several servers should hand them the same streams: torch's
         caching allocator keeps freed device memory per stream, so memory
-        cached for streams that are no longer used is not reused."""
+        cached for streams that are no longer used is not reused.
+        max_group_work: a group takes further jobs only while its work (pixels
+        of label jobs, site updates of sw jobs) stays within this bound, since
+        every job of a group is done when the whole group is; a job larger
+        than the bound runs as a group of its own."""
         import torch
         self.torch = torch
         self.clock = lambda: 0.0    # time since the start of run(), set by run()
@@ -161,6 +171,7 @@ class Server:
         slots = len(self.streams)
         self.free_slots = list(range(slots))
         self.max_group = max_group
+        self.max_group_work = max_group_work
         self.keep_results = keep_results
         self.queue = collections.deque()
         self.running = []
@@ -181,6 +192,7 @@ class Server:
         needs its bytes within the budget.  The first job that does not fit
         stops admission (first in, first out)."""
         groups = {"label": [], "sw": []}
+        work = {"label": 0, "sw": 0}
         while self.queue:
             job = self.queue[0]
             if job.bytes > self.budget:
@@ -191,12 +203,15 @@ class Server:
                 break
             if len(grp) >= self.max_group or self.in_use + job.bytes > self.budget:
                 break
+            if grp and work[job.kind] + job.work > self.max_group_work:
+                break
             if job.kind == "label":            # its labels' pinned host buffer
                 job.host_buf = self.pool.acquire(4 * job.H * job.W)
                 if job.host_buf is None:
                     break
             self.queue.popleft()
             self.in_use += job.bytes
+            work[job.kind] += job.work
             job.t_admit = now
             grp.append(job)
         self.peak_in_use = max(self.peak_in_use, self.in_use)

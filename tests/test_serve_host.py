@@ -1,7 +1,8 @@
 """Host logic of the serving loop (serve.Server) on the CPU: admission in
 arrival order under the HBM budget, one group per kind and step, each on a
-free slot, at most max_group jobs per group, and the release of memory and
-slots when a group completes.  Launches and CUDA events are stubs here; the
+free slot, at most max_group jobs and max_group_work pixels or site updates
+per group (one larger job alone), and the release of memory and slots when
+a group completes.  Launches and CUDA events are stubs here; the
 GPU tests run the real groups."""
 import collections
 
@@ -45,12 +46,13 @@ class _HostRows:
 class StubServer(serve.Server):
     """serve.Server's host state without CUDA streams; launches are recorded."""
 
-    def __init__(self, budget, slots=2, max_group=32):
+    def __init__(self, budget, slots=2, max_group=32, max_group_work=serve.MAX_GROUP_WORK):
         self.budget = int(budget)
         self.in_use = 0
         self.streams = [None] * slots
         self.free_slots = list(range(slots))
         self.max_group = max_group
+        self.max_group_work = max_group_work
         self.keep_results = False
         self.queue = collections.deque()
         self.running = []
@@ -117,6 +119,23 @@ def test_a_group_needs_a_free_slot_and_at_most_max_group_jobs(monkeypatch):
     assert s.launched[-1] == ("sw", [3])
     _finish_all(s, 0.4)
     assert s.idle() and [j.id for j in s.done] == [0, 1, 2, 3]
+
+
+def test_a_group_takes_jobs_while_its_work_is_within_the_bound(monkeypatch):
+    monkeypatch.setattr(serve.sw, "sw_batch_destroy", lambda b: None)
+    s = StubServer(1 << 40, slots=2, max_group_work=3 * 64 * 64)
+    # labels of 64^2 pixels: three fit one group; a 256^2 job is larger than
+    # the bound and runs as a group of its own
+    for j in [_label(0), _label(1), _label(2), _label(3), _label(4, side=256), _sw(5, L=128)]:
+        s.submit(j)
+    s.step(0.0)
+    assert s.launched == [("label", [0, 1, 2])]   # job 3 would exceed the bound; FIFO stops there
+    s.step(0.1)
+    assert s.launched[-1] == ("label", [3])       # the second slot; job 4 would exceed the bound
+    _finish_all(s, 0.2)
+    assert s.launched[-2:] == [("label", [4]), ("sw", [5])]   # larger than the bound: alone
+    _finish_all(s, 0.3)
+    assert s.idle() and [j.id for j in s.done] == [0, 1, 2, 3, 4, 5]
 
 
 def test_completion_releases_memory_and_slots():
