@@ -46,10 +46,13 @@ SWEEP_COUNTERS = {      # kernel: (DRAM bytes per site, warp instructions per si
     "k_sw_flip": ((216.697600 + 49.599232) * 1e6 / 67108864, 88898788 / 67108864),
 }
 # The stand-alone labeling call (k_ccl_tile, k_merge, k_ccl_final), one ncu
-# capture per kernel of a 4096^2 critical percolation mask: DRAM bytes per site.
+# capture per kernel of a 4096^2 critical percolation mask: DRAM bytes per site,
+# for the build with CCL_COUNTER_TILE_W-wide tiles, to which the binding routes
+# labeling.
 CCL_COUNTER_SOURCES = ("label_tile.cuh", "tile_engine.cuh", "k_label.cu", "swccl_device.cuh", "swccl_shared.h")
 CCL_COUNTER_HASH = "f484848673f87f5c"
-CCL_TRAFFIC_BYTES_PER_SITE = ((4.294912 + 19.587840) + (16.799232 + 0.000768) + (74.641408 + 8.061952)) * 1e6 / 16777216
+CCL_COUNTER_TILE_W = 128
+CCL_TRAFFIC_BYTES_PER_SITE = ((4.231680 + 19.281408) + (19.984640 + 0.001536) + (74.931456 + 8.132864)) * 1e6 / 16777216
 # Algorithmic HBM bytes per site: the fused sweep reads and writes the int8
 # spins once (2 B, the minimum of any sweep); the kernel split adds the
 # 16-bit tile roots written by k_sw_label and read by k_sw_flip (6 B).
@@ -85,7 +88,9 @@ def sweep_counters():
 
 
 def _ccl_traffic(N):
-    return CCL_TRAFFIC_BYTES_PER_SITE * N if sources_hash(CCL_COUNTER_SOURCES) == CCL_COUNTER_HASH else None
+    from paper_1105_5804_gb300 import _lib
+    ok = sources_hash(CCL_COUNTER_SOURCES) == CCL_COUNTER_HASH and _lib.CCL_TILE_W == CCL_COUNTER_TILE_W
+    return CCL_TRAFFIC_BYTES_PER_SITE * N if ok else None
 
 
 def _peaks():

@@ -29,10 +29,19 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def _gpu_label(mask_np, H, W, periodic):
+def _gpu_label(mask_np, H, W, periodic, tile_w=None):
+    """Labels through the binding (tile_w None: the build it routes labeling
+    to) or through the C ABI of the build with tile_w-wide tiles."""
     m = _dev(mask_np)
     lab = torch.full((H * W,), -7, dtype=torch.int32, device="cuda")
-    sw.ccl_label(m, lab, H, W, periodic)
+    if tile_w is None:
+        sw.ccl_label(m, lab, H, W, periodic)
+    else:
+        L = sw.lib(tile_w)
+        rc = L.ccl_label(ctypes.c_void_p(m.data_ptr()), ctypes.c_void_p(lab.data_ptr()), H, W,
+                         1 if periodic else 0, None)
+        assert rc == 0, L.sw_last_error()
+        torch.cuda.synchronize()
     sw.ccl_status()
     return lab.cpu().numpy()
 
@@ -52,6 +61,18 @@ def test_labels_random_masks(H, W, periodic, p):
     mask = inputs.random_mask(H, W, p, seed=H * 7919 + W * 31 + int(100 * p))
     ref, _ = oracle.label(mask, H, W, periodic)
     assert np.array_equal(_gpu_label(mask, H, W, periodic), ref)
+
+
+# every build's labeling (the binding routes stand-alone labeling to one of
+# them), on shapes that are ragged for each tile width
+@pytest.mark.parametrize("tile_w", sw.TILE_WIDTHS)
+@pytest.mark.parametrize("H,W", [(1, 1), (7, 1), (63, 127), (65, 129), (257, 129), (513, 385), (1000, 999)])
+@pytest.mark.parametrize("periodic", [True, False])
+def test_labels_every_tile_width(tile_w, H, W, periodic):
+    for p in (0.5, 0.62):
+        mask = inputs.random_mask(H, W, p, seed=H * 131 + W + int(100 * p))
+        ref, _ = oracle.label(mask, H, W, periodic)
+        assert np.array_equal(_gpu_label(mask, H, W, periodic, tile_w), ref), (tile_w, p)
 
 
 def test_labels_empty_and_full_masks():
