@@ -39,11 +39,11 @@ WORKLOAD = "sw_ising_q2_L%d_beta_c_hot_start_seed7"
 # reports null.
 SWEEP_COUNTER_SOURCES = ("fused_tile.cuh", "tile_engine.cuh", "k_fused.cu", "k_label.cu", "swccl_device.cuh",
                          "swccl_shared.h")
-SWEEP_COUNTER_HASH = "29dc69aefe68f8b0"
+SWEEP_COUNTER_HASH = "fd4886e2062ba574"
 SWEEP_COUNTERS = {      # kernel: (DRAM bytes per site, warp instructions per site)
-    "k_sw_label": ((94.317056 + 141.447168) * 1e6 / 67108864, 187235547 / 67108864),
-    "k_merge": ((78.398976 + 2.100224) * 1e6 / 67108864, 15475005 / 67108864),
-    "k_sw_flip": ((216.697600 + 49.599232) * 1e6 / 67108864, 88898788 / 67108864),
+    "k_sw_label": ((94.292224 + 141.398272) * 1e6 / 67108864, 187240592 / 67108864),
+    "k_merge": ((78.398208 + 2.086144) * 1e6 / 67108864, 15479167 / 67108864),
+    "k_sw_flip": ((216.637952 + 50.000384) * 1e6 / 67108864, 93617901 / 67108864),
 }
 # The stand-alone labeling call (k_ccl_tile, k_merge, k_ccl_final), one ncu
 # capture per kernel of a 4096^2 critical percolation mask: DRAM bytes per site,

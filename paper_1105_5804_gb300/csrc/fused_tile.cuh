@@ -651,7 +651,7 @@ __device__ __forceinline__ void sw_flip_whole_tile(const SwRep& R, int t, uint64
   __syncthreads();
 
   // 4. one draw per tile root, keyed by its cluster's final root
-  constexpr int U = 2;
+  constexpr int U = 4;   // four walks of a thread in flight (flip_tile_core, with the roots in registers, keeps two)
   for (int k0 = threadIdx.x; k0 < n_roots; k0 += U * LABEL_THREADS) {
     int r[U], Rg[U];
     bool act[U];
