@@ -39,20 +39,20 @@ WORKLOAD = "sw_ising_q2_L%d_beta_c_hot_start_seed7"
 # reports null.
 SWEEP_COUNTER_SOURCES = ("fused_tile.cuh", "tile_engine.cuh", "k_fused.cu", "k_label.cu", "swccl_device.cuh",
                          "swccl_shared.h")
-SWEEP_COUNTER_HASH = "fd4886e2062ba574"
+SWEEP_COUNTER_HASH = "a64f8956685ba9d7"
 SWEEP_COUNTERS = {      # kernel: (DRAM bytes per site, warp instructions per site)
-    "k_sw_label": ((94.292224 + 141.398272) * 1e6 / 67108864, 187240592 / 67108864),
-    "k_merge": ((78.398208 + 2.086144) * 1e6 / 67108864, 15479167 / 67108864),
-    "k_sw_flip": ((216.637952 + 50.000384) * 1e6 / 67108864, 93617901 / 67108864),
+    "k_sw_label": ((94.285824 + 141.310976) * 1e6 / 67108864, 187239060 / 67108864),
+    "k_merge": ((78.399488 + 2.301952) * 1e6 / 67108864, 16679698 / 67108864),
+    "k_sw_flip": ((216.701440 + 50.096128) * 1e6 / 67108864, 93623845 / 67108864),
 }
 # The stand-alone labeling call (k_ccl_tile, k_merge, k_ccl_final), one ncu
 # capture per kernel of a 4096^2 critical percolation mask: DRAM bytes per site,
 # for the build with CCL_COUNTER_TILE_W-wide tiles, to which the binding routes
 # labeling.
 CCL_COUNTER_SOURCES = ("label_tile.cuh", "tile_engine.cuh", "k_label.cu", "swccl_device.cuh", "swccl_shared.h")
-CCL_COUNTER_HASH = "f484848673f87f5c"
+CCL_COUNTER_HASH = "e77db4595e4b212e"
 CCL_COUNTER_TILE_W = 128
-CCL_TRAFFIC_BYTES_PER_SITE = ((4.231680 + 19.281408) + (19.984640 + 0.001536) + (74.931456 + 8.132864)) * 1e6 / 16777216
+CCL_TRAFFIC_BYTES_PER_SITE = ((4.231680 + 19.404032) + (19.985920 + 0.001536) + (74.935808 + 8.063232)) * 1e6 / 16777216
 # Algorithmic HBM bytes per site: the fused sweep reads and writes the int8
 # spins once (2 B, the minimum of any sweep); the kernel split adds the
 # 16-bit tile roots written by k_sw_label and read by k_sw_flip (6 B).

@@ -250,27 +250,36 @@ __device__ __forceinline__ void merge_seam_bond(int32_t* gpar, const Grid& g, co
   int a = -1, b = -1;
   bool valid = false;
   if (active) {
+    // the bond's bit and the roots at both ends are loaded together (the
+    // neighbour index wraps, so the loads stay inside the records even
+    // where the bond does not exist), then the bit decides
     const int ty = t / g.tiles_x, tx = t - ty * g.tiles_x;
     const int32_t* rec = s.seams + (int64_t)t * SeamLayout::INTS;
+    bool has;
+    int tn, i_bits, i_a, i_b, bit;
     if (k < TILE_H) {
-      const bool has_east = g.periodic || tx + 1 < g.tiles_x;
-      const uint32_t ebits = (uint32_t)__ldcg(rec + SeamLayout::E_BITS + (k >> 5));
-      if (has_east && ((ebits >> (k & 31)) & 1u)) {
-        const int te = ty * g.tiles_x + (tx + 1 == g.tiles_x ? 0 : tx + 1);
-        a = __ldcg(rec + SeamLayout::COL_R + k);
-        b = __ldcg(s.seams + (int64_t)te * SeamLayout::INTS + SeamLayout::COL_L + k);
-        valid = true;
-      }
+      has = g.periodic || tx + 1 < g.tiles_x;
+      tn = ty * g.tiles_x + (tx + 1 == g.tiles_x ? 0 : tx + 1);
+      i_bits = SeamLayout::E_BITS + (k >> 5);
+      i_a = SeamLayout::COL_R + k;
+      i_b = SeamLayout::COL_L + k;
+      bit = k & 31;
     } else {
       const int lx = k - TILE_H;
-      const bool has_north = g.periodic || ty + 1 < g.tiles_y;
-      const uint32_t nbits = (uint32_t)__ldcg(rec + SeamLayout::N_BITS + (lx >> 5));
-      if (has_north && ((nbits >> (lx & 31)) & 1u)) {
-        const int tn = (ty + 1 == g.tiles_y ? 0 : ty + 1) * g.tiles_x + tx;
-        a = __ldcg(rec + SeamLayout::ROW_T + lx);
-        b = __ldcg(s.seams + (int64_t)tn * SeamLayout::INTS + SeamLayout::ROW_B + lx);
-        valid = true;
-      }
+      has = g.periodic || ty + 1 < g.tiles_y;
+      tn = (ty + 1 == g.tiles_y ? 0 : ty + 1) * g.tiles_x + tx;
+      i_bits = SeamLayout::N_BITS + (lx >> 5);
+      i_a = SeamLayout::ROW_T + lx;
+      i_b = SeamLayout::ROW_B + lx;
+      bit = lx & 31;
+    }
+    const uint32_t bits = (uint32_t)__ldcg(rec + i_bits);
+    const int ra = __ldcg(rec + i_a);
+    const int rb = __ldcg(s.seams + (int64_t)tn * SeamLayout::INTS + i_b);
+    if (has && ((bits >> bit) & 1u)) {
+      a = ra;
+      b = rb;
+      valid = true;
     }
   }
   valid = valid && a != b;
