@@ -21,7 +21,10 @@
 //              other root is its own final root; each root draws its
 //              cluster's new state once
 //              (FLIP draw keyed by R, Sec. II.D) and every site copies the
-//              state of its tile root.
+//              state of its tile root.  When every tile is whole (L a
+//              multiple of TILE_W), k_sw_flip_whole does the same without
+//              bounds checks, reading a thread's tile roots twice through L2
+//              instead of holding them in registers across the draws.
 //
 // HBM traffic per site: spins read 1 B, 16-bit roots written and read 4 B,
 // spins written 1 B, plus seam records and edge-root entries.
