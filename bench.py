@@ -671,10 +671,13 @@ def run_ours(args):
     # end to end through the C ABI with host buffers: every step uploads its
     # input spins from pinned host memory, sweeps once, and reads its
     # observables and spins back to pinned host memory.  Two variants:
-    #  - synchronous: the calls one after another, host buffers passed directly;
-    #  - pipelined (the line's e2e): the same calls on device staging buffers,
-    #    the host<->device copies on their own streams, double-buffered, so the
-    #    upload of step k+1 and the download of step k-1 overlap step k.
+    #  - synchronous: sw_set_spins, sw_sweep, sw_observables, sw_get_spins one
+    #    after another, host buffers passed directly;
+    #  - pipelined (the line's e2e): one sw_sweep_io per step on device
+    #    staging buffers (input checked on the device, observables written to
+    #    pinned host memory, nothing waits for the device), the host<->device
+    #    copies on their own streams, double-buffered, so the upload of step
+    #    k+1 and the download of step k-1 overlap step k.
     # Every step's bytes cross the host link inside the timed region.
     e2e_steps = 0 if args.no_e2e else max(3, min(args.steps, 20))
     host_in = [torch.empty(N, dtype=torch.int8).pin_memory() for _ in range(2)]
@@ -692,9 +695,11 @@ def run_ours(args):
     te_sync = max_over_ranks(time.perf_counter() - te0)
     dev_in = [torch.empty(N, dtype=torch.int8, device="cuda") for _ in range(2)]
     dev_out = [torch.empty(N, dtype=torch.int8, device="cuda") for _ in range(2)]
+    obs_host = torch.zeros((max(e2e_steps, 1), q + 1), dtype=torch.int64).pin_memory()
     up, down = torch.cuda.Stream(), torch.cuda.Stream()
     cs = torch.cuda.ExternalStream(sw.sw_stream(h))
     ev_up = [torch.cuda.Event() for _ in range(2)]
+    ev_comp = [torch.cuda.Event() for _ in range(2)]
     ev_down = [torch.cuda.Event() for _ in range(2)]
     barrier()
     torch.cuda.synchronize()
@@ -707,20 +712,22 @@ def run_ours(args):
         b = k % 2
         if k + 1 < e2e_steps:                       # next step's input goes up meanwhile
             with torch.cuda.stream(up):
+                if k >= 1:
+                    up.wait_event(ev_comp[1 - b])   # step k-1 has read dev_in[1 - b]
                 dev_in[1 - b].copy_(host_in[1 - b], non_blocking=True)
                 ev_up[1 - b].record(up)
         cs.wait_event(ev_up[b])
-        sw.sw_set_spins(h, dev_in[b])
-        sw.sw_sweep(h, 1)
-        o = sw.sw_observables(h, 1)
         if k >= 2:
-            ev_down[b].synchronize()                # dev_out[b]'s previous download done
-        sw.sw_get_spins(h, dev_out[b])
+            cs.wait_event(ev_down[b])               # dev_out[b]'s previous download done
+        sw.sw_sweep_io(h, 1, inp=dev_in[b], obs_out=obs_host[k], out=dev_out[b])
+        ev_comp[b].record(cs)
         with torch.cuda.stream(down):               # this step's result comes down meanwhile
+            down.wait_event(ev_comp[b])
             host_out[b].copy_(dev_out[b], non_blocking=True)
             ev_down[b].record(down)
     torch.cuda.synchronize()
     te = max_over_ranks(time.perf_counter() - te0)
+    sw.sw_sync(h)                                   # device status of the pipelined steps
     e2e_value = world * N * e2e_steps / (te * 1e9) if e2e_steps else None
 
     secondary = {}
@@ -822,10 +829,12 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": "site-updates/ns", "h2d_bytes_per_step": N,
                 "d2h_bytes_per_step": N + 8 * (q + 1), "steps": e2e_steps,
                 "synchronous_value": world * N * e2e_steps / (te_sync * 1e9) if e2e_steps else None,
-                "path": "per step: sw_set_spins + sw_sweep(1) + sw_observables + sw_get_spins on device staging "
-                        "buffers; spins up from and down to pinned host memory on two copy streams, double-buffered "
-                        "(upload of step k+1 and download of step k-1 overlap step k); synchronous_value: the same "
-                        "calls on the host buffers directly, one after another"},
+                "path": "per step: one sw_sweep_io (input spins from a device staging buffer, checked on the "
+                        "device; one sweep; its observables to pinned host memory; the spins to a device staging "
+                        "buffer; no host wait); spins up from and down to pinned host memory on two copy streams, "
+                        "double-buffered (upload of step k+1 and download of step k-1 overlap step k); "
+                        "synchronous_value: sw_set_spins + sw_sweep(1) + sw_observables + sw_get_spins on the host "
+                        "buffers directly, one after another"},
         "roofline": roofline,
         "hbm_view": hbm_view,
         "kernels": kernels,

@@ -154,6 +154,25 @@ int sw_get_spins(sw_handle* h, int8_t* dst, int is_device);
  * next sweep.  Synchronises. */
 int sw_set_spins(sw_handle* h, const int8_t* src, int is_device);
 
+/* One step of a pipeline, fully asynchronous on the handle's stream (no call
+ * in it waits for the device):
+ *  - in != NULL: device memory, int8[L*L]; the spins are replaced by it if
+ *    every value is in [0, q) (checked on the device, as sw_set_spins), else
+ *    they stay unchanged and SW_ERR_ARG is noted in the handle's device
+ *    status word, returned once by the next call that reads it (sw_sync,
+ *    sw_observables, sw_get_spins).  The input must stay valid until the
+ *    stream has passed this call.
+ *  - n sweeps (0 <= n <= 4096), as sw_sweep.
+ *  - obs_out != NULL (and n > 0): the observables of these n sweeps, n rows
+ *    of 1 + q int64 as in sw_observables, written to obs_out (pinned host or
+ *    device memory) in stream order; they count as read.
+ *  - out != NULL: device memory, int8[L*L], receives the spins after the
+ *    sweeps.
+ * Results are ready when the stream reaches the end of the call (an event
+ * recorded on sw_stream(h), or sw_sync).  Returns SW_OK, or SW_ERR_ARG /
+ * SW_ERR_CUDA for what the host can see when enqueueing. */
+int sw_sweep_io(sw_handle* h, const int8_t* in, int n, int64_t* obs_out, int8_t* out);
+
 /* Copy the bond mask (ceil(L*L/4) bytes, packed as above) and the canonical
  * labels (int32[L*L]) of the last completed sweep, for bit-exact checks.
  * Either pointer may be NULL.  SW_ERR_STATE if the last sweep did not run in

@@ -11,7 +11,7 @@ from ._lib import (  # noqa: F401
     SW_CONV_AUTO, SW_CONV_POTTS, SW_CONV_ISING, SW_N_PHASES, PHASE_NAMES, SW_MODE_STAGED, SW_MODE_FUSED,
     SwcclError, lib, mask_bytes,
     sw_last_error, sw_threshold_for, sw_create, sw_create_ex, sw_create_threshold, sw_destroy,
-    sw_sweep, sw_sync, sw_observables, sw_get_spins, sw_set_spins, sw_debug_dump, sw_get_info,
+    sw_sweep, sw_sync, sw_observables, sw_get_spins, sw_set_spins, sw_sweep_io, sw_debug_dump, sw_get_info,
     sw_stream, sw_set_timing, sw_phase_times, sw_set_mode, SW_UPDATE_SW, SW_UPDATE_FEW, sw_set_update,
     sw_prob_threshold,
     ccl_label, ccl_workspace_bytes, ccl_label_ws, ccl_bonds_from_pixels, ccl_perc_mask, ccl_status,

@@ -63,6 +63,7 @@ def lib(tile_w=256):
         "sw_observables": ([vp, vp, i32, ctypes.POINTER(i32)], i32),
         "sw_get_spins": ([vp, vp, i32], i32),
         "sw_set_spins": ([vp, vp, i32], i32),
+        "sw_sweep_io": ([vp, vp, i32, vp, vp], i32),
         "sw_debug_dump": ([vp, vp, vp, i32], i32),
         "sw_get_info": ([vp, vp], i32),
         "sw_stream": ([vp], vp),
@@ -246,6 +247,28 @@ def sw_set_spins(h, src):
         if a.size != N:
             raise ValueError("need %d spins" % N)
         _check(lib().sw_set_spins(h, a.ctypes.data, 0))
+
+
+def sw_sweep_io(h, n, inp=None, obs_out=None, out=None):
+    """One asynchronous pipeline step (see include/swccl.h): inp (CUDA int8
+    tensor of L*L spins or None) replaces the spins if valid, n sweeps run,
+    their observables go to obs_out (int64 tensor of n x (1+q), pinned host
+    or CUDA, or None) and the spins to out (CUDA int8 tensor or None).
+    Nothing waits for the device."""
+    import torch
+    L, q = _Lq(h)
+    N = L * L
+    ip = _dev(inp, torch.int8, N, "inp") if inp is not None else None
+    op = _dev(out, torch.int8, N, "out") if out is not None else None
+    if obs_out is not None:
+        if obs_out.dtype != torch.int64 or not obs_out.is_contiguous() or obs_out.numel() < n * (q + 1):
+            raise ValueError("obs_out must be a contiguous int64 tensor of at least n x (1 + q) elements")
+        if not obs_out.is_cuda and not obs_out.is_pinned():
+            raise ValueError("obs_out must be pinned host memory or a CUDA tensor")
+        obs_ptr = ctypes.c_void_p(obs_out.data_ptr())
+    else:
+        obs_ptr = None
+    _check(lib().sw_sweep_io(_handle(h), ip, n, obs_ptr, op))
 
 
 def sw_debug_dump(h, mask_out=None, labels_out=None):

@@ -217,6 +217,18 @@ cudaError_t launch_copy_if(int8_t* dst, const int8_t* src, int64_t n, const int*
   return cudaGetLastError();
 }
 
+// A check's failure code (flag != 0) is recorded in a status word; the
+// first code there stays.
+__global__ void k_note_error(const int* __restrict__ flag, int* err) {
+  const int f = *flag;
+  if (threadIdx.x == 0 && f != 0) atomicCAS(err, 0, f);
+}
+
+cudaError_t launch_note_error(const int* flag, int* err, cudaStream_t st) {
+  k_note_error<<<1, 32, 0, st>>>(flag, err);
+  return cudaGetLastError();
+}
+
 }  // namespace swccl
 
 namespace swccl {

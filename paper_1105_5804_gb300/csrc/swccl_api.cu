@@ -18,6 +18,11 @@
 
 #include "swccl_shared.h"
 
+namespace swccl {
+// k_bonds.cu: a nonzero *flag is recorded in *err (the first code stays)
+cudaError_t launch_note_error(const int* flag, int* err, cudaStream_t st);
+}  // namespace swccl
+
 using namespace swccl;
 
 namespace {
@@ -203,6 +208,12 @@ cudaError_t read_small(sw_handle* h, void* dst, const void* src, size_t bytes) {
 int check_device_status(sw_handle* h) {
   SwCtl c;
   CK(read_small(h, &c, h->ctl, sizeof(c)));
+  if (c.err == SW_ERR_ARG) {
+    // only sw_sweep_io records this code: an input it rejected, leaving the
+    // spins unchanged; reported once
+    CK(cudaMemsetAsync(reinterpret_cast<char*>(h->ctl) + offsetof(SwCtl, err), 0, sizeof(int), h->stream));
+    return fail(SW_ERR_ARG, "sw_sweep_io: an input spin value was outside [0, q); the spins were left unchanged");
+  }
   if (c.err) return fail(c.err, "a device-side consistency check failed in a sweep");
   return SW_OK;
 }
@@ -471,6 +482,42 @@ int sw_set_spins(sw_handle* h, const int8_t* src, int is_device) {
   int bad = 0;
   CK(read_small(h, &bad, h->chk, sizeof(int)));
   if (bad) return fail(SW_ERR_ARG, "sw_set_spins: spin value outside [0, q)");
+  return SW_OK;
+}
+
+int sw_sweep_io(sw_handle* h, const int8_t* in, int n, int64_t* obs_out, int8_t* out) {
+  if (!h || n < 0 || n > OBS_CAP) return fail(SW_ERR_ARG, "sw_sweep_io: bad arguments");
+  const int64_t N = (int64_t)h->L * h->L;
+  const cudaStream_t st = h->stream;
+  if (in) {
+    // the observables still pending belong to the spins being replaced; the
+    // input goes in only if every value is valid, else the code is noted in
+    // the status word (read by the next synchronising call)
+    CK(finish_observables(h));
+    CK(cudaMemsetAsync(h->chk, 0, sizeof(int), st));
+    CK(launch_check_spins(in, N, h->q, h->chk, st));
+    CK(launch_copy_if(h->spins, in, N, h->chk, st));
+    CK(launch_note_error(h->chk, h->ls.err, st));
+    h->dump_valid = false;
+  }
+  if (n > 0) {
+    const int rc = sw_sweep(h, n);
+    if (rc) return rc;
+  }
+  if (obs_out && n > 0) {
+    CK(finish_observables(h));
+    const int row = h->q + 1;
+    int64_t done = 0;
+    const uint64_t first = h->sweeps - (uint64_t)n;
+    while (done < n) {
+      const int64_t slot = (int64_t)((first + done) % OBS_CAP);
+      const int64_t run = std::min<int64_t>(n - done, OBS_CAP - slot);
+      CK(cudaMemcpyAsync(obs_out + done * row, h->obs + slot * row, run * row * 8, cudaMemcpyDefault, st));
+      done += run;
+    }
+    h->obs_read = h->sweeps;
+  }
+  if (out) CK(launch_copy_if(out, h->spins, N, nullptr, st));
   return SW_OK;
 }
 

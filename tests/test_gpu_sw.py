@@ -414,3 +414,58 @@ def test_fused_L16384_one_step_equivalence(q, beta, conv):
     finally:
         sw.sw_destroy(hf)
         sw.sw_destroy(hs)
+
+
+# sw_sweep_io: the asynchronous pipeline step (input spins, sweeps, their
+# observables and the output spins, no host wait) against the oracle chain
+@pytest.mark.parametrize("L,q", [(36, 3), (256, 2), (260, 4)])
+def test_sweep_io_matches_the_chain(L, q):
+    T = oracle.threshold(oracle.coupling_K(q, math.log(1 + math.sqrt(q)), 1.0, oracle.CONV_POTTS))
+    seed = 77 + L
+    h = sw.sw_create_threshold(L, q, T, seed, True)
+    try:
+        s = oracle.init_spins(L, q, seed, True)
+        done = 0
+        rng = np.random.default_rng(L)
+        out = torch.empty(L * L, dtype=torch.int8, device="cuda")
+        for n, new_input in [(3, False), (1, True), (0, True), (4, False), (2, True)]:
+            inp = None
+            if new_input:
+                s = rng.integers(0, q, L * L).astype(np.int8)
+                inp = torch.from_numpy(s).cuda()
+            obs = torch.zeros((max(n, 1), 1 + q), dtype=torch.int64).pin_memory()
+            sw.sw_sweep_io(h, n, inp=inp, obs_out=obs if n else None, out=out)
+            sw.sw_sync(h)
+            s, ref = oracle.chain(L, q, T, seed, done, n, s)
+            done += n
+            assert np.array_equal(out.cpu().numpy(), s), (L, q, done)
+            if n:
+                assert np.array_equal(obs.numpy()[:n], ref), (L, q, done)
+        # the rows count as read: nothing is left for sw_observables
+        assert sw.sw_observables(h, 4096).shape[0] == 0
+        assert np.array_equal(sw.sw_get_spins(h), s)
+    finally:
+        sw.sw_destroy(h)
+
+
+def test_sweep_io_rejects_bad_input_on_the_device():
+    L, q = 64, 3
+    T = oracle.threshold(oracle.coupling_K(q, math.log(1 + math.sqrt(q)), 1.0, oracle.CONV_POTTS))
+    h = sw.sw_create_threshold(L, q, T, 5, True)
+    try:
+        sw.sw_sweep(h, 2)
+        before = sw.sw_get_spins(h)
+        bad = torch.zeros(L * L, dtype=torch.int8, device="cuda")
+        bad[L * L // 2] = q                       # one value outside [0, q)
+        sw.sw_sweep_io(h, 0, inp=bad)             # enqueued: no error yet
+        with pytest.raises(sw.SwcclError) as e:
+            sw.sw_sync(h)
+        assert e.value.code == sw.SW_ERR_ARG
+        sw.sw_sync(h)                             # reported once
+        assert np.array_equal(sw.sw_get_spins(h), before)
+        # the chain goes on from the spins it kept
+        s, _ = oracle.chain(L, q, T, 5, 2, 1, before)
+        sw.sw_sweep(h, 1)
+        assert np.array_equal(sw.sw_get_spins(h), s)
+    finally:
+        sw.sw_destroy(h)
