@@ -113,3 +113,12 @@ def test_batch_barrier_limit_refuses_bad_arguments(lib):
     lib.sw_batch_set_barrier_limit.argtypes = [ctypes.c_void_p, ctypes.c_longlong]
     lib.sw_batch_set_barrier_limit.restype = ctypes.c_int
     assert lib.sw_batch_set_barrier_limit(None, 0) == 1          # SW_ERR_ARG
+
+
+def test_sweep_io_refuses_bad_arguments_on_the_host():
+    """sw_sweep_io checks its handle and sweep count before touching the
+    device (this runs without a GPU)."""
+    from paper_1105_5804_gb300 import _lib
+    L = _lib.lib()
+    assert L.sw_sweep_io(None, None, 1, None, None) == _lib.SW_ERR_ARG
+    assert "sw_sweep_io" in L.sw_last_error().decode()
