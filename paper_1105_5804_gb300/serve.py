@@ -112,7 +112,7 @@ def pinned_pool(arena_bytes=12 << 30):
     return _POOLS[arena_bytes]
 
 
-MAX_GROUP_WORK = 32 << 20         # pixels or site updates of one group (one job may exceed it)
+MAX_GROUP_WORK = 8 << 20          # pixels or site updates of one group (one job may exceed it)
 
 
 class Job:
