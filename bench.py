@@ -50,9 +50,9 @@ SWEEP_COUNTERS = {      # kernel: (DRAM bytes per site, warp instructions per si
 # for the build with CCL_COUNTER_TILE_W-wide tiles, to which the binding routes
 # labeling.
 CCL_COUNTER_SOURCES = ("label_tile.cuh", "tile_engine.cuh", "k_label.cu", "swccl_device.cuh", "swccl_shared.h")
-CCL_COUNTER_HASH = "e77db4595e4b212e"
+CCL_COUNTER_HASH = "2c55f8edeccf7c13"
 CCL_COUNTER_TILE_W = 128
-CCL_TRAFFIC_BYTES_PER_SITE = ((4.231680 + 19.404032) + (19.985920 + 0.001536) + (74.935808 + 8.063232)) * 1e6 / 16777216
+CCL_TRAFFIC_BYTES_PER_SITE = ((7.725056 + 5.867776) + (19.986176 + 0.001280) + (59.200256 + 10.390016)) * 1e6 / 16777216
 # Algorithmic HBM bytes per site: the fused sweep reads and writes the int8
 # spins once (2 B, the minimum of any sweep); the kernel split adds the
 # 16-bit tile roots written by k_sw_label and read by k_sw_flip (6 B).

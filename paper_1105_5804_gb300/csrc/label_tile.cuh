@@ -26,12 +26,14 @@ __device__ __forceinline__ uint32_t even_bits(unsigned long long x) {
 // writes every site's label (global index of its tile root, the minimum
 // site index of its tile component), the tile's root list, and the seam
 // record (labels and outgoing bond bits of the four tile edges).
-// LOCAL (the stand-alone labeling path, finished by final_labels_tile): a
-// site that is not its tile's root gets -(r + 1), r its tile root's local
-// index, instead of the root's global index, and the root list holds local
-// indices, with CCL_EDGE_ROOT set on the roots whose component reaches the
-// tile edge.  Only tile roots' entries are global parent pointers, so the
-// seam merge and root lookups, which walk tile roots only, are unchanged.
+// LOCAL (the stand-alone labeling path, finished by final_labels_tile): the
+// label array receives only the parent entries of the tile roots whose
+// component reaches the tile edge (label = own global index), which the
+// seam merge and the final root walks use; every site's tile root goes, as
+// a 16-bit local index, to the tile's hook-log slot (free once the engine
+// has ended), in tile row-major order; the root list holds local indices,
+// with CCL_EDGE_ROOT set on the edge roots.  final_labels_tile writes every
+// site's label.
 constexpr int CCL_EDGE_ROOT = 1 << 30;
 template <bool LOCAL = false>
 __device__ __forceinline__ void ccl_label_tile(const uint8_t* __restrict__ mask, int32_t* __restrict__ labels,
@@ -94,19 +96,41 @@ __device__ __forceinline__ void ccl_label_tile(const uint8_t* __restrict__ mask,
     __syncthreads();
   }
 
-  // 4b. every site's root; global labels; root list
+  // 4b. every site's root; root list.  LOCAL: the roots as 16-bit local
+  //     indices into the tile's hook-log slot (free since the engine ended),
+  //     four consecutive sites per thread and step (lane-consecutive words of
+  //     par); mine bit j: site 4 (threadIdx.x + (j / 4) LABEL_THREADS) + j % 4.
+  //     Otherwise global labels; mine bit j: site threadIdx.x + j LABEL_THREADS.
   constexpr int PER_T = TILE_SITES / LABEL_THREADS;
-  uint32_t mine = 0;      // bit j: site threadIdx.x + j*LABEL_THREADS is a root
+  uint32_t mine = 0;
+  if (LOCAL) {
+    uint16_t* lr = reinterpret_cast<uint16_t*>(hook_log);
+#pragma unroll 2
+    for (int j = 0; j < PER_T / 4; ++j) {
+      const int sidx = 4 * ((int)threadIdx.x + j * LABEL_THREADS);
+      const int ly = sidx >> TILE_W_LOG2, lx = sidx & (TILE_W - 1);
+      if (ly >= h) continue;   // rows past the grid: the engine wrote no entries there
+      const int4 pv = *reinterpret_cast<const int4*>(&par[sidx]);
+      const int r0 = par[pv.x], r1 = par[pv.y], r2 = par[pv.z], r3 = par[pv.w];
+      *reinterpret_cast<uint2*>(lr + sidx) =
+          make_uint2((uint32_t)r0 | ((uint32_t)r1 << 16), (uint32_t)r2 | ((uint32_t)r3 << 16));
+      // columns past the grid (bondless, each its own root) are no roots of the tile
+      const uint32_t in = lx + 4 <= w ? 0xFu : (lx < w ? (1u << (w - lx)) - 1u : 0u);
+      const uint32_t is_root = (uint32_t)(r0 == sidx) | ((uint32_t)(r1 == sidx + 1) << 1) |
+                               ((uint32_t)(r2 == sidx + 2) << 2) | ((uint32_t)(r3 == sidx + 3) << 3);
+      mine |= (is_root & in) << (4 * j);
+    }
+  } else {
 #pragma unroll 4
-  for (int j = 0; j < PER_T; ++j) {
-    const int sidx = threadIdx.x + j * LABEL_THREADS;
-    const int ly = sidx >> TILE_W_LOG2, lx = sidx & (TILE_W - 1);
-    if (ly < h && lx < w) {
-      const int p = par[sidx];
-      const int r = par[p];
-      labels[(int64_t)(y0 + ly) * W + x0 + lx] =
-          (LOCAL && r != sidx) ? -(r + 1) : (y0 + (r >> TILE_W_LOG2)) * W + x0 + (r & (TILE_W - 1));
-      if (r == sidx) mine |= 1u << j;
+    for (int j = 0; j < PER_T; ++j) {
+      const int sidx = threadIdx.x + j * LABEL_THREADS;
+      const int ly = sidx >> TILE_W_LOG2, lx = sidx & (TILE_W - 1);
+      if (ly < h && lx < w) {
+        const int p = par[sidx];
+        const int r = par[p];
+        labels[(int64_t)(y0 + ly) * W + x0 + lx] = (y0 + (r >> TILE_W_LOG2)) * W + x0 + (r & (TILE_W - 1));
+        if (r == sidx) mine |= 1u << j;
+      }
     }
   }
   int cnt = __popc(mine), incl = cnt;
@@ -128,9 +152,19 @@ __device__ __forceinline__ void ccl_label_tile(const uint8_t* __restrict__ mask,
   while (mine) {
     const int j = __ffs(mine) - 1;
     mine &= mine - 1;
-    const int sidx = threadIdx.x + j * LABEL_THREADS;
-    slot[base++] = LOCAL ? (sidx | (((edge[sidx >> 5] >> (sidx & 31)) & 1u) ? CCL_EDGE_ROOT : 0))
-                         : (y0 + (sidx >> TILE_W_LOG2)) * W + x0 + (sidx & (TILE_W - 1));
+    if (LOCAL) {
+      // an edge root's label entry is its parent entry for the seam merge
+      const int sidx = 4 * ((int)threadIdx.x + (j >> 2) * LABEL_THREADS) + (j & 3);
+      const bool on_edge = (edge[sidx >> 5] >> (sidx & 31)) & 1u;
+      if (on_edge) {
+        const int32_t gr = (y0 + (sidx >> TILE_W_LOG2)) * W + x0 + (sidx & (TILE_W - 1));
+        labels[gr] = gr;
+      }
+      slot[base++] = sidx | (on_edge ? CCL_EDGE_ROOT : 0);
+    } else {
+      const int sidx = threadIdx.x + j * LABEL_THREADS;
+      slot[base++] = (y0 + (sidx >> TILE_W_LOG2)) * W + x0 + (sidx & (TILE_W - 1));
+    }
   }
 
   // 5. seam record
@@ -193,9 +227,9 @@ __device__ __forceinline__ void site_compress_tile(int32_t* __restrict__ labels,
 }
 
 // Final labels of tile t for the stand-alone path (after the seam merge, on
-// labels written by ccl_label_tile<true>): each tile root (local root list)
-// finds its cluster root R on the label array and stores it in `table` at
-// its local index; then every site of the tile takes table[its tile root].
+// what ccl_label_tile<true> wrote): each tile root (local root list) finds
+// its cluster root R on the label array and stores it in `table` at its
+// local index; then every site of the tile takes table[its tile root].
 // A tile root's entry receives R (smaller than any value other walks may
 // store there), so walks of other tiles through it stay valid.  All threads
 // of the CTA call it; it synchronises the CTA.
@@ -227,35 +261,30 @@ __device__ __forceinline__ void final_labels_tile(int32_t* labels, const Grid& g
       if (k0 + u * (int)blockDim.x < n) table[r[u]] = x[u];
   }
   __syncthreads();
-  // 2. every site takes its tile root's cluster root: four sites per 16-byte
-  //    word when rows start 16-byte aligned (a 16-byte aligned array and
-  //    W % 4 == 0; x0 is a multiple of 256)
+  // 2. every site takes its tile root's cluster root; the tile roots are the
+  //    16-bit local indices ccl_label_tile<true> left in the tile's hook-log
+  //    slot, eight sites per 16-byte word, in tile row-major order; labels go
+  //    out four sites per 16-byte store when rows start 16-byte aligned (a
+  //    16-byte aligned array and W % 4 == 0; x0 is a multiple of TILE_W, so w
+  //    is a multiple of 4 too)
+  const uint16_t* lr = reinterpret_cast<const uint16_t*>(s.work + (int64_t)t * TILE_SITES);
   if ((g.W & 3) == 0 && (reinterpret_cast<uintptr_t>(labels) & 15) == 0) {
-    for (int k = threadIdx.x; k < TILE_SITES / 4; k += blockDim.x) {
-      const int sidx = 4 * k;
+    for (int k = threadIdx.x; k < TILE_SITES / 8; k += blockDim.x) {
+      const int sidx = 8 * k;
       const int ly = sidx >> TILE_W_LOG2, lx = sidx & (TILE_W - 1);
       if (ly >= h || lx >= w) continue;
+      const uint4 v = __ldcg(reinterpret_cast<const uint4*>(lr + sidx));
       int32_t* p = labels + (int64_t)(y0 + ly) * g.W + x0 + lx;
-      if (lx + 4 <= w) {
-        const int4 v = __ldcg(reinterpret_cast<const int4*>(p));
-        const int4 o = make_int4(table[v.x < 0 ? -v.x - 1 : sidx], table[v.y < 0 ? -v.y - 1 : sidx + 1],
-                                 table[v.z < 0 ? -v.z - 1 : sidx + 2], table[v.w < 0 ? -v.w - 1 : sidx + 3]);
-        *reinterpret_cast<int4*>(p) = o;
-      } else {
-        for (int j = 0; lx + j < w; ++j) {
-          const int v = __ldcg(p + j);
-          p[j] = table[v < 0 ? -v - 1 : sidx + j];
-        }
-      }
+      *reinterpret_cast<int4*>(p) =
+          make_int4(table[v.x & 0xFFFFu], table[v.x >> 16], table[v.y & 0xFFFFu], table[v.y >> 16]);
+      if (lx + 8 <= w)
+        *reinterpret_cast<int4*>(p + 4) =
+            make_int4(table[v.z & 0xFFFFu], table[v.z >> 16], table[v.w & 0xFFFFu], table[v.w >> 16]);
     }
   } else {
     for (int k = threadIdx.x; k < TILE_SITES; k += blockDim.x) {
       const int ly = k >> TILE_W_LOG2, lx = k & (TILE_W - 1);
-      if (ly < h && lx < w) {
-        int32_t* p = labels + (int64_t)(y0 + ly) * g.W + x0 + lx;
-        const int v = __ldcg(p);
-        *p = table[v < 0 ? -v - 1 : k];
-      }
+      if (ly < h && lx < w) labels[(int64_t)(y0 + ly) * g.W + x0 + lx] = table[__ldcg(lr + k)];
     }
   }
   __syncthreads();
