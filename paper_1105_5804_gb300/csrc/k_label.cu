@@ -28,11 +28,12 @@
 //                 cluster's new state here (Sec. II.D), keyed by the root.
 //  k_site_compress  label[i] = label[label[i]] for every site (the staged
 //                 sweep's dump of canonical labels).
-// The stand-alone labeling (launch_ccl) uses k_ccl_tile, a k_tile_label whose
-// non-root sites hold their tile root's local index (negated), then k_merge,
-// then k_ccl_final: per tile, each tile root finds its cluster root once and
-// every site takes its tile root's from a shared-memory table -- one pass
-// over the labels instead of a root pass and a site pass with gathers.
+// The stand-alone labeling (launch_ccl) uses k_ccl_tile, a k_tile_label that
+// keeps every site's tile root as a 16-bit local index in the tile's scratch
+// and writes label entries only for the tile roots on the tile edge (their
+// parent entries), then k_merge, then k_ccl_final: per tile, each tile root
+// finds its cluster root once and every site takes its tile root's from a
+// shared-memory table -- every label written once, no gathers.
 #include "label_tile.cuh"
 
 namespace swccl {
